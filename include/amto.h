@@ -1,0 +1,204 @@
+/*
+ * amto.h - C ABI of the B300 (sm_103a) alternating-minimisation multi-agent
+ * trajectory optimiser of Rastgar et al., "GPU Accelerated Convex
+ * Approximations for Fast Multi-Agent Trajectory Optimization" (arXiv
+ * 2011.04240).
+ *
+ * The library computes Algorithm 1 of the paper: per iteration, the x/y/z
+ * QPs (Eqs. step_x_3d-step_z_3d) through a cached inverse of the KKT matrix
+ * (Eq. kkt_step_x, Remarks 1-2), the closed-form alpha/beta projection
+ * (Eq. sphere_project), the d step clipped to d >= 1 (Eq. step_d and
+ * Eq. alpha_beta_constr) and the multiplier update (Eq. lag_update), for a
+ * batch of independent planning instances that share one agent count.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  "device" pointers are CUDA device (or managed)
+ *     memory of the current device; "host" pointers are ordinary host
+ *     memory.  The caller owns every buffer it passes in; the plan owns its
+ *     cached inverse and its workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous on it: outputs
+ *     are valid once the stream has been synchronised.
+ *   - No C++ exception and no abort crosses this boundary.  Every call
+ *     returns an amto_status; amto_last_error() gives a thread-local text.
+ *   - Agent-major layouts: xi is [batch][3 axes][n][deg+1] float32, with the
+ *     Bernstein coefficients of agent i, axis ax at xi[(b*3+ax)*n*(deg+1) +
+ *     i*(deg+1) + k] (the stacking c_x of Sec. III-B).
+ *   - Pairs are the unordered pairs (i, j), i < j, numbered i-major
+ *     (q = 0 for (0,1), 1 for (0,2), ...), the row order of Eq. (A_f);
+ *     the pair difference is Delta = position_i - position_j.
+ */
+#ifndef AMTO_H
+#define AMTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amto_plan_s* amto_plan;
+
+typedef enum {
+    AMTO_OK = 0,
+    AMTO_EINVAL = 1,      /* invalid argument (message says which) */
+    AMTO_ENOMEM = 2,      /* device or pinned-host allocation failed */
+    AMTO_ECUDA = 3,       /* a CUDA runtime call failed */
+    AMTO_ENONFINITE = 4,  /* non-finite input or state */
+    AMTO_ETIMEOUT = 5,    /* a bounded device wait ran out */
+    AMTO_ENUMERIC = 6     /* the KKT inverse failed its self-check */
+} amto_status;
+
+/* Where lambda enters the alpha/beta/d steps (reading of Eqs. sphere_project
+ * and step_d). */
+enum {
+    AMTO_PROJ_LITERAL = 0,  /* alpha, beta from Delta; d step with lambda^k / rho */
+    AMTO_PROJ_NOLAMBDA = 1  /* lambda only in b_fc (Eq. b_f) and Eq. lag_update */
+};
+
+/* Arithmetic of the cached-inverse apply.  The pair projection is float32
+ * in every mode. */
+enum {
+    AMTO_PREC_FP32 = 0,     /* float32 SIMT */
+    AMTO_PREC_TF32X3 = 1,   /* tensor cores, hi/lo split, 3 products, fp32 accumulate */
+    AMTO_PREC_BF16X3 = 2,   /* tensor cores, hi/lo split, 3 products, fp32 accumulate */
+    AMTO_PREC_TF32 = 3,     /* tensor cores, single product */
+    AMTO_PREC_BF16 = 4      /* tensor cores, single product */
+};
+
+/* Boundary-condition bits (rows of A in Sec. III-B). */
+enum {
+    AMTO_BC_POS0 = 1, AMTO_BC_VEL0 = 2, AMTO_BC_ACC0 = 4,
+    AMTO_BC_POST = 8, AMTO_BC_VELT = 16, AMTO_BC_ACCT = 32,
+    AMTO_BC_ALL = 63
+};
+
+typedef struct {
+    int n_agents;      /* n, 2 <= n <= 256 */
+    int m_steps;       /* samples per trajectory, poly_degree + 1 <= m <= 4096 */
+    int poly_degree;   /* Bernstein degree N, 2 <= N <= 15 (N+1 coefficients) */
+    double T;          /* horizon in seconds, > 0; samples t_k = k T / (m-1) */
+    double a;          /* spheroid semi-axis l_xy, > 0 */
+    double b;          /* spheroid semi-axis l_z, > 0 */
+    double rho;        /* augmented-Lagrangian weight, > 0 */
+    unsigned bc_mask;  /* AMTO_BC_* bits; must contain POS0 and POST */
+    int proj_mode;     /* AMTO_PROJ_* */
+    int precision;     /* AMTO_PREC_* */
+    int max_batch;     /* largest batch a solve may take, >= 1 */
+} amto_params;
+
+typedef struct {
+    int n_agents, m_steps, nv, nb;      /* nv = N+1 coefficients, nb = #BC rows */
+    int kkt_dim;                        /* (nv + nb) * n */
+    int group;                          /* agents per lane group of the pair kernel */
+    int t_chunk;                        /* time samples per pair-kernel block */
+    int n_chunks;                       /* pair-kernel blocks per instance */
+    long long lambda_floats;            /* float32 multiplier slots per instance (one buffer) */
+    double kkt_check;                   /* max |K K^-1 - I| of the FP64 inverse */
+    size_t device_bytes;                /* device memory owned by the plan */
+} amto_info;
+
+/*
+ * amto_create - build a plan for one agent count (Remarks 1-2: the KKT
+ * matrix depends on n, rho and the basis only, so its inverse is computed
+ * once and reused for any start/goal).
+ *
+ * On the current CUDA device: forms the Bernstein basis P, Pdot, Pddot
+ * (Eq. param), Q_x, A, A_eq and the KKT matrix of Eq. (kkt_step_x), inverts
+ * it by Gauss-Jordan elimination with partial pivoting in FP64, checks
+ * max|K K^-1 - I|, and keeps the top block rows of the inverse in float32.
+ * Allocates all device workspace for `max_batch` instances, so amto_solve
+ * allocates nothing.  Synchronous.  Errors: EINVAL for out-of-range
+ * params, ENOMEM, ECUDA, ENUMERIC if the inverse fails its self-check.
+ * *out is NULL on error.
+ */
+amto_status amto_create(const amto_params* params, amto_plan* out);
+
+/* Release the plan and all device memory it owns.  NULL is a no-op.
+ * Synchronises the device work the plan issued. */
+void amto_destroy(amto_plan plan);
+
+/*
+ * amto_solve - run Algorithm 1 on `batch` instances (1 <= batch <= max_batch).
+ *
+ *   start, goal  device [batch][n][3] float32: positions at t = 0 and t = T
+ *                (b_eq of Sec. III-B).
+ *   bc_extra     device [batch][n][2][2][3] float32 or NULL: [t0 | T]
+ *                [velocity | acceleration][axis] boundary values (zero when
+ *                NULL).
+ *   xi_init      device [batch][3][n][N+1] float32 or NULL: warm-start
+ *                trajectories; NULL = smoothness-only initialisation.
+ *   lambda_init  device [batch][3][p][m] float32 or NULL (p = n(n-1)/2,
+ *                pair-major then time): warm-start multipliers; NULL = 0.
+ *   max_iters    >= 0 iterations (QP solves) at most.
+ *   tol          stop an instance once its max over pairs and samples of
+ *                ||f_c||_2 (Eq. sphere_proposed) is below tol after at
+ *                least one iteration; 0 = run max_iters.
+ *   xi_out       device [batch][3][n][N+1] float32: final trajectories.
+ *   resid_out    device [batch] float32 or NULL: final max ||f_c||_2,
+ *                recomputed in FP64 from the final trajectories and
+ *                multipliers; NaN for an instance with non-finite input.
+ *   iters_out    device [batch] int32 or NULL: iterations performed; -1 for
+ *                an instance with non-finite input or state.
+ *
+ * The whole iteration loop runs on the device (a CUDA graph with a
+ * device-side loop condition); nothing is allocated after the first solve
+ * of a given batch size (which instantiates that graph).  Errors: EINVAL
+ * (sizes, NULL required pointers), ECUDA.  Non-convergence is not an
+ * error: iters_out = max_iters and the residual is reported.
+ */
+amto_status amto_solve(amto_plan plan, int batch,
+                       const float* start, const float* goal, const float* bc_extra,
+                       const float* xi_init, const float* lambda_init,
+                       int max_iters, float tol,
+                       float* xi_out, float* resid_out, int* iters_out,
+                       void* stream);
+
+/*
+ * amto_get_state - read back the multipliers of the last solve on this plan
+ * and alpha, beta, d of its last projection (Eqs. sphere_project, step_d).
+ * All outputs are device pointers, each may be NULL:
+ *   lambda_out [batch][3][p][m], alpha_out/beta_out/d_out [batch][p][m],
+ * float32.  `batch` must equal the last solve's batch.  Asynchronous.
+ */
+amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out,
+                           float* alpha_out, float* beta_out, float* d_out,
+                           void* stream);
+
+/* Sizes and self-check figures of a plan (host struct, synchronous). */
+amto_status amto_get_info(amto_plan plan, amto_info* out);
+
+/*
+ * amto_get_kkt_inverse - copy the FP64 KKT inverse, (nv+nb)n x (nv+nb)n
+ * row-major, unknowns ordered [c (agent-major) ; multipliers (agent-major)],
+ * to host memory `out` (kkt_dim^2 doubles).  Synchronous.
+ */
+amto_status amto_get_kkt_inverse(amto_plan plan, double* out);
+
+/*
+ * amto_get_stats - per-kernel device time of the most recent traced solve
+ * (see amto_set_trace): out_ms[k] total milliseconds and out_count[k]
+ * launches for k = 0 pair kernel, 1 rhs kernel, 2 apply kernel.  Host
+ * arrays of length 3.
+ */
+amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count);
+
+/*
+ * amto_set_trace - 1: later solves launch each kernel from a host loop and
+ * bracket it with CUDA events on the solve's stream (per-kernel timing, no
+ * graph, one host synchronisation per iteration); 0: graph mode (default).
+ * Results are identical in both modes.
+ */
+amto_status amto_set_trace(amto_plan plan, int on);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* amto_last_error(void);
+
+/* Library version string. */
+const char* amto_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMTO_H */

@@ -1,0 +1,251 @@
+"""Python binding of the amto C ABI (include/amto.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels of libamto.so.  This module
+loads the in-tree library with ctypes and raises ImportError if it has not
+been built; there is no other implementation to fall back to.
+
+The low-level functions mirror the C entry points one to one (same names
+without the ``amto_`` prefix) and take raw device pointers.  ``Planner`` is a
+convenience wrapper that passes torch tensors' device pointers and the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamto.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC = range(7)
+PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
+BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
+
+STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",
+                4: "AMTO_ENONFINITE", 5: "AMTO_ETIMEOUT", 6: "AMTO_ENUMERIC"}
+
+
+class AmtoError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int), ("m_steps", ctypes.c_int),
+                ("poly_degree", ctypes.c_int), ("T", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("rho", ctypes.c_double),
+                ("bc_mask", ctypes.c_uint), ("proj_mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int), ("m_steps", ctypes.c_int), ("nv", ctypes.c_int),
+                ("nb", ctypes.c_int), ("kkt_dim", ctypes.c_int), ("group", ctypes.c_int),
+                ("t_chunk", ctypes.c_int), ("n_chunks", ctypes.c_int),
+                ("lambda_floats", ctypes.c_longlong), ("kkt_check", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "amto_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    "amto_destroy": (None, [_P]),
+    "amto_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int,
+                                  ctypes.c_float, _P, _P, _P, _P]),
+    "amto_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "amto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "amto_get_kkt_inverse": (ctypes.c_int, [_P, _P]),
+    "amto_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "amto_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
+    "amto_last_error": (ctypes.c_char_p, []),
+    "amto_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libamto.so (once).  Raises ImportError when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libamto.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise AmtoError(status, load().amto_last_error().decode())
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+# ----------------------------------------------------------------------------
+# One-to-one wrappers of the C entry points
+# ----------------------------------------------------------------------------
+
+def create(params: Params) -> int:
+    plan = _P()
+    _check(load().amto_create(ctypes.byref(params), ctypes.byref(plan)))
+    return plan.value
+
+
+def destroy(plan: int) -> None:
+    if plan:
+        load().amto_destroy(plan)
+
+
+def solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init, max_iters, tol,
+          xi_out, resid_out, iters_out, stream) -> None:
+    _check(load().amto_solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init,
+                             max_iters, tol, xi_out, resid_out, iters_out, stream))
+
+
+def get_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, stream) -> None:
+    _check(load().amto_get_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, stream))
+
+
+def get_info(plan) -> Info:
+    info = Info()
+    _check(load().amto_get_info(plan, ctypes.byref(info)))
+    return info
+
+
+def get_kkt_inverse(plan, out_ptr) -> None:
+    _check(load().amto_get_kkt_inverse(plan, out_ptr))
+
+
+def get_stats(plan):
+    ms = (ctypes.c_double * 3)()
+    cnt = (ctypes.c_int * 3)()
+    _check(load().amto_get_stats(plan, ms, cnt))
+    return list(ms), list(cnt)
+
+
+def set_trace(plan, on: bool) -> None:
+    _check(load().amto_set_trace(plan, 1 if on else 0))
+
+
+def last_error() -> str:
+    return load().amto_last_error().decode()
+
+
+def version() -> str:
+    return load().amto_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# torch convenience wrapper (device memory and streams only)
+# ----------------------------------------------------------------------------
+
+class Planner:
+    """A plan for one agent count; solves batches of start/goal sets on the GPU.
+
+    All tensors are float32 CUDA tensors on the plan's device.  Solves run on
+    torch's current stream unless `stream` is given.
+    """
+
+    def __init__(self, n_agents: int, m_steps: int, T: float, a: float = 0.6, b: float = 1.2,
+                 rho: float = 1.0, poly_degree: int = 10, bc_mask: int = BC_ALL,
+                 proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
+                 max_batch: int = 1):
+        import torch
+        self._torch = torch
+        self.plan = None
+        self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
+                             proj_mode, precision, max_batch)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.plan = create(self.params)
+        self.info = get_info(self.plan)
+        self.n, self.m, self.nv = n_agents, m_steps, poly_degree + 1
+        self.p = n_agents * (n_agents - 1) // 2
+        self.last_batch = 0
+
+    def close(self):
+        if self.plan:
+            destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self._torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def _check_tensor(self, t, shape, name, dtype=None):
+        torch = self._torch
+        dtype = dtype or torch.float32
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"{name}: expected contiguous {dtype} CUDA tensor of shape {shape}, "
+                             f"got {tuple(t.shape)} {t.dtype} on {t.device}")
+        return t
+
+    def solve(self, start, goal, max_iters: int, tol: float = 0.0, bc_extra=None,
+              xi_init=None, lambda_init=None, out=None, stream=None):
+        """Run Algorithm 1; returns (xi [B,3,n,nv], resid [B], iters [B])."""
+        torch = self._torch
+        B = start.shape[0]
+        n, nv = self.n, self.nv
+        self._check_tensor(start, (B, n, 3), "start")
+        self._check_tensor(goal, (B, n, 3), "goal")
+        self._check_tensor(bc_extra, (B, n, 2, 2, 3), "bc_extra")
+        self._check_tensor(xi_init, (B, 3, n, nv), "xi_init")
+        self._check_tensor(lambda_init, (B, 3, self.p, self.m), "lambda_init")
+        if out is None:
+            xi = torch.empty((B, 3, n, nv), device=self.device, dtype=torch.float32)
+            resid = torch.empty((B,), device=self.device, dtype=torch.float32)
+            iters = torch.empty((B,), device=self.device, dtype=torch.int32)
+        else:
+            xi, resid, iters = out
+        solve(self.plan, B, _ptr(start), _ptr(goal), _ptr(bc_extra), _ptr(xi_init),
+              _ptr(lambda_init), int(max_iters), float(tol), _ptr(xi), _ptr(resid),
+              _ptr(iters), self._stream(stream))
+        self.last_batch = B
+        return xi, resid, iters
+
+    def state(self, stream=None):
+        """(lambda [B,3,p,m], alpha, beta, d [B,p,m]) of the last solve."""
+        torch = self._torch
+        B = self.last_batch
+        lam = torch.empty((B, 3, self.p, self.m), device=self.device, dtype=torch.float32)
+        al = torch.empty((B, self.p, self.m), device=self.device, dtype=torch.float32)
+        be = torch.empty_like(al)
+        d = torch.empty_like(al)
+        get_state(self.plan, B, _ptr(lam), _ptr(al), _ptr(be), _ptr(d), self._stream(stream))
+        return lam, al, be, d
+
+    def kkt_inverse(self):
+        import numpy as np
+        k = self.info.kkt_dim
+        out = np.empty((k, k), dtype=np.float64)
+        get_kkt_inverse(self.plan, out.ctypes.data)
+        return out
+
+    def set_trace(self, on: bool):
+        set_trace(self.plan, on)
+
+    def stats(self):
+        return get_stats(self.plan)

@@ -1,0 +1,128 @@
+// Internal declarations of the amto library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+
+#include "amto.h"
+
+namespace amto {
+
+// ---------------------------------------------------------------------------
+// Error handling: a thread-local message, no exceptions across the ABI.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+
+#define AMTO_CUDA_TRY(call)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (call);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            ::amto::set_error(std::string(#call " failed: ") + cudaGetErrorString(_e)); \
+            return AMTO_ECUDA;                                                     \
+        }                                                                          \
+    } while (0)
+
+// Flags per instance (device int).
+enum : int { FLAG_DONE = 1, FLAG_APPLY = 2, FLAG_NONFINITE = 4 };
+
+// Kernel kinds traced by amto_get_stats.
+enum : int { KSTAT_PAIR = 0, KSTAT_RHS = 1, KSTAT_APPLY = 2, KSTAT_N = 3 };
+
+// Device-side control block of a solve.
+struct Ctl {
+    int max_iters;
+    float tol;
+    int batch;
+    unsigned int ticket;        // last-block detection in the rhs kernel
+    unsigned int active;        // running count of active instances this pass
+    unsigned int active_last;   // active count after the last rhs pass
+};
+
+// Geometry of the pair kernel's work decomposition (see iterate.cu).
+struct PairGeom {
+    int G;          // agents per lane group (power of two, 2..32)
+    int TPW;        // time samples per warp pass = 32 / G
+    int nbk;        // agent blocks = ceil(n / G)
+    int npad;       // nbk * G
+    int S;          // steps per time group = nbk^2 G / 2
+    int warps;      // warps per block
+    int QW;         // time groups per warp
+    int QC;         // time groups per block = warps * QW
+    int TC;         // time samples per block = QC * TPW
+    int n_chunks;   // blocks per instance = ceil(m / TC)
+    int MQ;         // time groups per instance = n_chunks * QC
+    long long lam_floats;  // multiplier floats per instance and buffer = MQ * S * 3 * 32
+};
+
+PairGeom choose_geometry(int n, int m);
+
+struct Graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+};
+
+}  // namespace amto
+
+struct amto_plan_s {
+    amto_params prm;
+    int device = 0;
+    int n = 0, m = 0, N = 0, nv = 0, nb = 0, kdim = 0, p = 0;
+    amto::PairGeom geo{};
+    double kkt_check = 0.0;
+    size_t bytes = 0;
+
+    // constants (device)
+    float* P32 = nullptr;      // [m][nv]
+    double* P64 = nullptr;     // [m][nv]
+    float* Q32 = nullptr;      // [nv][nv]  Pddot^T Pddot
+    float* A32 = nullptr;      // [nb][nv]
+    float* E0 = nullptr;       // [nv][nb]  top-right block of the agent-level inverse
+    double* Kinv64 = nullptr;  // [kdim][kdim]
+    float* Ktop = nullptr;     // [n nv][kdim]
+
+    // state for max_batch instances (device)
+    float* xi = nullptr;       // [B][3][n nv]
+    float* beq = nullptr;      // [B][3][n nb]
+    float* lam[2] = {nullptr, nullptr};  // [B][lam_floats]
+    float* gpart = nullptr;    // [B][n_chunks][3][n nv]
+    float* rpart = nullptr;    // [B][n_chunks]
+    float* rhs = nullptr;      // [B][3][kdim]
+    float* rmax = nullptr;     // [B]
+    unsigned long long* r64 = nullptr;  // [B] FP64 final residual^2 bits
+    int* iters = nullptr;      // [B]
+    int* flags = nullptr;      // [B]
+    amto::Ctl* ctl = nullptr;
+    amto::Ctl* ctl_host = nullptr;   // pinned mirror for host polling
+
+    int last_batch = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::map<int, amto::Graph> graphs;
+
+    // tracing
+    int trace = 0;
+    double stat_ms[amto::KSTAT_N] = {0, 0, 0};
+    int stat_cnt[amto::KSTAT_N] = {0, 0, 0};
+};
+
+namespace amto {
+// precompute.cu
+amto_status precompute(amto_plan_s* pl);
+// iterate.cu
+amto_status configure_kernels(amto_plan_s* pl);
+amto_status launch_setup(amto_plan_s* pl, int batch, const float* start, const float* goal,
+                         const float* bc_extra, const float* xi_init, int max_iters, float tol,
+                         cudaStream_t s);
+amto_status launch_pair(amto_plan_s* pl, int batch, int init_mode, const float* lambda_init,
+                        cudaStream_t s);
+amto_status launch_rhs(amto_plan_s* pl, int batch, cudaGraphConditionalHandle h, int use_cond,
+                       cudaStream_t s);
+amto_status launch_apply(amto_plan_s* pl, int batch, cudaStream_t s);
+amto_status launch_final(amto_plan_s* pl, int batch, float* xi_out, float* resid_out,
+                         int* iters_out, cudaStream_t s);
+amto_status launch_state(amto_plan_s* pl, int batch, float* lambda_out, float* alpha_out,
+                         float* beta_out, float* d_out, cudaStream_t s);
+}  // namespace amto

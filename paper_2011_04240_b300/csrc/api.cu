@@ -1,0 +1,370 @@
+// C ABI entry points (include/amto.h): validation, plan memory, the solve
+// sequence and its CUDA graph with a device-side loop condition.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "amto_internal.cuh"
+
+namespace amto {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+amto_status einval(const char* what) {
+    set_error(std::string("invalid argument: ") + what);
+    return AMTO_EINVAL;
+}
+
+template <typename T>
+amto_status dalloc(amto_plan_s* pl, T** ptr, size_t count) {
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)ptr, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed");
+        return AMTO_ENOMEM;
+    }
+    pl->bytes += sizeof(T) * count;
+    return AMTO_OK;
+}
+
+void free_plan(amto_plan_s* pl) {
+    if (!pl) return;
+    for (auto& kv : pl->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    pl->graphs.clear();
+    void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kinv64, pl->Ktop,
+                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
+                    pl->rmax, pl->r64, pl->iters, pl->flags, pl->ctl};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (pl->ctl_host) cudaFreeHost(pl->ctl_host);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    delete pl;
+}
+
+amto_status build_graph(amto_plan_s* pl, int batch, Graph& out) {
+    Graph g;
+    AMTO_CUDA_TRY(cudaGraphCreate(&g.graph, 0));
+    auto fail = [&](amto_status st) {
+        if (g.graph) cudaGraphDestroy(g.graph);
+        return st;
+    };
+    if (cudaGraphConditionalHandleCreate(&g.handle, g.graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGraphConditionalHandleCreate failed");
+        return fail(AMTO_ECUDA);
+    }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = g.handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGraphAddNode (while) failed");
+        return fail(AMTO_ECUDA);
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(pl->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaStreamBeginCaptureToGraph failed");
+        return fail(AMTO_ECUDA);
+    }
+    amto_status st = launch_rhs(pl, batch, g.handle, 1, pl->cap_stream);
+    if (st == AMTO_OK) st = launch_apply(pl, batch, pl->cap_stream);
+    if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, pl->cap_stream);
+    cudaGraph_t captured = body;
+    cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &captured);
+    if (st != AMTO_OK) return fail(st);
+    if (ce != cudaSuccess) {
+        set_error(std::string("stream capture of the iteration failed: ") + cudaGetErrorString(ce));
+        return fail(AMTO_ECUDA);
+    }
+    if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaGraphInstantiate failed");
+        return fail(AMTO_ECUDA);
+    }
+    out = g;
+    return AMTO_OK;
+}
+
+// Host-driven loop with CUDA events around every launch (amto_set_trace).
+amto_status run_traced(amto_plan_s* pl, int batch, int max_iters, cudaStream_t s) {
+    cudaEvent_t ev[5];
+    for (auto& e : ev) AMTO_CUDA_TRY(cudaEventCreate(&e));
+    amto_status st = AMTO_OK;
+    for (int it = 0; it <= max_iters + 1 && st == AMTO_OK; ++it) {
+        cudaEventRecord(ev[0], s);
+        st = launch_rhs(pl, batch, 0, 0, s);
+        cudaEventRecord(ev[1], s);
+        if (st != AMTO_OK) break;
+        cudaMemcpyAsync(pl->ctl_host, pl->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("traced solve: stream synchronisation failed");
+            st = AMTO_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        pl->stat_ms[KSTAT_RHS] += ms;
+        pl->stat_cnt[KSTAT_RHS] += 1;
+        if (pl->ctl_host->active_last == 0) break;
+        cudaEventRecord(ev[2], s);
+        st = launch_apply(pl, batch, s);
+        cudaEventRecord(ev[3], s);
+        if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, s);
+        cudaEventRecord(ev[4], s);
+        if (cudaEventSynchronize(ev[4]) != cudaSuccess) {
+            set_error("traced solve: event synchronisation failed");
+            st = AMTO_ECUDA;
+            break;
+        }
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        pl->stat_ms[KSTAT_APPLY] += ms;
+        pl->stat_cnt[KSTAT_APPLY] += 1;
+        cudaEventElapsedTime(&ms, ev[3], ev[4]);
+        pl->stat_ms[KSTAT_PAIR] += ms;
+        pl->stat_cnt[KSTAT_PAIR] += 1;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return st;
+}
+
+}  // namespace
+}  // namespace amto
+
+using namespace amto;
+
+extern "C" {
+
+const char* amto_last_error(void) { return g_last_error.c_str(); }
+
+const char* amto_version(void) { return "amto 0.1 (sm_103a)"; }
+
+amto_status amto_create(const amto_params* prm, amto_plan* out) {
+    clear_error();
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (!prm) return einval("params is NULL");
+    const amto_params& p = *prm;
+    if (p.n_agents < 2 || p.n_agents > 256) return einval("n_agents must be in [2, 256]");
+    if (p.poly_degree < 2 || p.poly_degree > 15) return einval("poly_degree must be in [2, 15]");
+    if (p.m_steps < p.poly_degree + 1 || p.m_steps > 4096)
+        return einval("m_steps must be in [poly_degree + 1, 4096]");
+    if (!(p.T > 0) || !std::isfinite(p.T)) return einval("T must be > 0");
+    if (!(p.a > 0) || !std::isfinite(p.a) || !(p.b > 0) || !std::isfinite(p.b))
+        return einval("a and b must be > 0");
+    if (!(p.rho > 0) || !std::isfinite(p.rho)) return einval("rho must be > 0");
+    if ((p.bc_mask & ~63u) || !(p.bc_mask & AMTO_BC_POS0) || !(p.bc_mask & AMTO_BC_POST))
+        return einval("bc_mask must be a subset of AMTO_BC_ALL containing POS0 and POST");
+    const int nb = __builtin_popcount(p.bc_mask);
+    if (nb >= p.poly_degree + 1) return einval("more boundary conditions than coefficients");
+    if (p.proj_mode != AMTO_PROJ_LITERAL && p.proj_mode != AMTO_PROJ_NOLAMBDA)
+        return einval("proj_mode");
+    if (p.precision != AMTO_PREC_FP32)
+        return einval("precision: only AMTO_PREC_FP32 is available in this build");
+    if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
+
+    amto_plan_s* pl = new (std::nothrow) amto_plan_s();
+    if (!pl) {
+        set_error("host allocation failed");
+        return AMTO_ENOMEM;
+    }
+    pl->prm = p;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        set_error("no CUDA device");
+        return AMTO_ECUDA;
+    }
+    pl->n = p.n_agents;
+    pl->m = p.m_steps;
+    pl->N = p.poly_degree;
+    pl->nv = p.poly_degree + 1;
+    pl->nb = nb;
+    pl->kdim = pl->n * (pl->nv + pl->nb);
+    pl->p = pl->n * (pl->n - 1) / 2;
+    pl->geo = choose_geometry(pl->n, pl->m);
+    const int B = p.max_batch, n = pl->n, nv = pl->nv, kdim = pl->kdim;
+    const size_t nvn = (size_t)n * nv;
+
+    amto_status st = AMTO_OK;
+    if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaStreamCreate failed");
+        st = AMTO_ECUDA;
+    }
+#define ALLOC(ptr, count) \
+    if (st == AMTO_OK) st = dalloc(pl, &(ptr), (count))
+    ALLOC(pl->P32, (size_t)pl->m * nv);
+    ALLOC(pl->P64, (size_t)pl->m * nv);
+    ALLOC(pl->Q32, (size_t)nv * nv);
+    ALLOC(pl->A32, (size_t)nb * nv);
+    ALLOC(pl->E0, (size_t)nv * nb);
+    ALLOC(pl->Kinv64, (size_t)kdim * kdim);
+    ALLOC(pl->Ktop, nvn * kdim);
+    ALLOC(pl->xi, (size_t)B * 3 * nvn);
+    ALLOC(pl->beq, (size_t)B * 3 * n * nb);
+    ALLOC(pl->lam[0], (size_t)B * pl->geo.lam_floats);
+    ALLOC(pl->lam[1], (size_t)B * pl->geo.lam_floats);
+    ALLOC(pl->gpart, (size_t)B * pl->geo.n_chunks * 3 * nvn);
+    ALLOC(pl->rpart, (size_t)B * pl->geo.n_chunks);
+    ALLOC(pl->rhs, (size_t)B * 3 * kdim);
+    ALLOC(pl->rmax, (size_t)B);
+    ALLOC(pl->r64, (size_t)B);
+    ALLOC(pl->iters, (size_t)B);
+    ALLOC(pl->flags, (size_t)B);
+    ALLOC(pl->ctl, (size_t)1);
+#undef ALLOC
+    if (st == AMTO_OK && cudaMallocHost((void**)&pl->ctl_host, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocHost failed");
+        st = AMTO_ENOMEM;
+    }
+    if (st == AMTO_OK) st = configure_kernels(pl);
+    if (st == AMTO_OK) st = precompute(pl);
+    if (st == AMTO_OK && cudaMemset(pl->flags, 0, sizeof(int) * B) != cudaSuccess) {
+        set_error("cudaMemset failed");
+        st = AMTO_ECUDA;
+    }
+    if (st == AMTO_OK && cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("device error during plan creation");
+        st = AMTO_ECUDA;
+    }
+    if (st != AMTO_OK) {
+        std::string keep = g_last_error;
+        free_plan(pl);
+        set_error(keep);
+        return st;
+    }
+    *out = pl;
+    return AMTO_OK;
+}
+
+void amto_destroy(amto_plan plan) {
+    if (!plan) return;
+    DeviceGuard g(plan->device);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+amto_status amto_solve(amto_plan plan, int batch, const float* start, const float* goal,
+                       const float* bc_extra, const float* xi_init, const float* lambda_init,
+                       int max_iters, float tol, float* xi_out, float* resid_out,
+                       int* iters_out, void* stream) {
+    clear_error();
+    if (!plan) return einval("plan is NULL");
+    if (batch < 1 || batch > plan->prm.max_batch) return einval("batch must be in [1, max_batch]");
+    if (!start || !goal || !xi_out) return einval("start, goal and xi_out are required");
+    if (max_iters < 0) return einval("max_iters must be >= 0");
+    if (!(tol >= 0.f) || !std::isfinite(tol)) return einval("tol must be a finite value >= 0");
+    DeviceGuard g(plan->device);
+    if (!g.ok) {
+        set_error("cannot select the plan's device");
+        return AMTO_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    amto_status st = launch_setup(plan, batch, start, goal, bc_extra, xi_init, max_iters, tol, s);
+    if (st != AMTO_OK) return st;
+    st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, s);
+    if (st != AMTO_OK) return st;
+    if (plan->trace) {
+        for (int k = 0; k < KSTAT_N; ++k) {
+            plan->stat_ms[k] = 0.0;
+            plan->stat_cnt[k] = 0;
+        }
+        st = run_traced(plan, batch, max_iters, s);
+    } else {
+        auto it = plan->graphs.find(batch);
+        if (it == plan->graphs.end()) {
+            Graph gr;
+            st = build_graph(plan, batch, gr);
+            if (st != AMTO_OK) return st;
+            it = plan->graphs.emplace(batch, gr).first;
+        }
+        AMTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+    }
+    if (st != AMTO_OK) return st;
+    st = launch_final(plan, batch, xi_out, resid_out, iters_out, s);
+    plan->last_batch = batch;
+    return st;
+}
+
+amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out, float* alpha_out,
+                           float* beta_out, float* d_out, void* stream) {
+    clear_error();
+    if (!plan) return einval("plan is NULL");
+    if (batch < 1 || batch != plan->last_batch)
+        return einval("batch must equal the last solve's batch");
+    DeviceGuard g(plan->device);
+    return launch_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, (cudaStream_t)stream);
+}
+
+amto_status amto_get_info(amto_plan plan, amto_info* out) {
+    clear_error();
+    if (!plan || !out) return einval("plan and out are required");
+    out->n_agents = plan->n;
+    out->m_steps = plan->m;
+    out->nv = plan->nv;
+    out->nb = plan->nb;
+    out->kkt_dim = plan->kdim;
+    out->group = plan->geo.G;
+    out->t_chunk = plan->geo.TC;
+    out->n_chunks = plan->geo.n_chunks;
+    out->lambda_floats = plan->geo.lam_floats;
+    out->kkt_check = plan->kkt_check;
+    out->device_bytes = plan->bytes;
+    return AMTO_OK;
+}
+
+amto_status amto_get_kkt_inverse(amto_plan plan, double* out) {
+    clear_error();
+    if (!plan || !out) return einval("plan and out are required");
+    DeviceGuard g(plan->device);
+    AMTO_CUDA_TRY(cudaMemcpy(out, plan->Kinv64, sizeof(double) * (size_t)plan->kdim * plan->kdim,
+                             cudaMemcpyDeviceToHost));
+    return AMTO_OK;
+}
+
+amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count) {
+    clear_error();
+    if (!plan || !out_ms || !out_count) return einval("plan, out_ms and out_count are required");
+    for (int k = 0; k < KSTAT_N; ++k) {
+        out_ms[k] = plan->stat_ms[k];
+        out_count[k] = plan->stat_cnt[k];
+    }
+    return AMTO_OK;
+}
+
+amto_status amto_set_trace(amto_plan plan, int on) {
+    clear_error();
+    if (!plan) return einval("plan is NULL");
+    plan->trace = on ? 1 : 0;
+    return AMTO_OK;
+}
+
+}  // extern "C"
