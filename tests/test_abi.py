@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/amto.h declares, and rejects invalid arguments before touching the
+GPU (host-side validation only; no compute call needs a device here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "amto.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(amto_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_04240_b300 import amto
+    return amto.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["amto_create", "amto_solve", "amto_destroy", "amto_get_state",
+                     "amto_get_info", "amto_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2011_04240_b300 import amto
+    assert set(_declared_functions()) <= set(amto.SIGNATURES)
+
+
+def _params(**kw):
+    from paper_2011_04240_b300 import amto
+    base = dict(n_agents=4, m_steps=50, poly_degree=10, T=5.0, a=0.6, b=1.2, rho=1.0,
+                bc_mask=63, proj_mode=0, precision=0, max_batch=1)
+    base.update(kw)
+    return amto.Params(**base)
+
+
+@pytest.mark.parametrize("bad", [dict(n_agents=1), dict(n_agents=300), dict(m_steps=5),
+                                 dict(poly_degree=1), dict(T=0.0), dict(a=-1.0),
+                                 dict(b=float("nan")), dict(rho=0.0), dict(bc_mask=0b001000),
+                                 dict(bc_mask=64 | 63), dict(proj_mode=7), dict(max_batch=0),
+                                 dict(precision=9)])
+def test_create_rejects_invalid_params(lib, bad):
+    from paper_2011_04240_b300 import amto
+    plan = ctypes.c_void_p()
+    st = lib.amto_create(ctypes.byref(_params(**bad)), ctypes.byref(plan))
+    assert st == amto.EINVAL
+    assert plan.value is None
+    assert "invalid argument" in lib.amto_last_error().decode()
+
+
+def test_null_arguments_rejected(lib):
+    from paper_2011_04240_b300 import amto
+    assert lib.amto_create(None, None) == amto.EINVAL
+    assert lib.amto_solve(None, 1, None, None, None, None, None, 1, 0.0, None, None, None,
+                          None) == amto.EINVAL
+    assert lib.amto_get_info(None, None) == amto.EINVAL
+    assert lib.amto_set_trace(None, 1) == amto.EINVAL
+    lib.amto_destroy(None)  # no-op
+    assert lib.amto_version().decode().startswith("amto")

@@ -1,0 +1,178 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the FP64
+oracle on the same seeded inputs.
+
+Tolerance: the normwise relative trajectory error
+max|xi_gpu - xi_oracle| / max|xi_oracle| must stay <= 1e-4 at every checked
+iteration k up to the problem's parity horizon (the float32 path follows the
+FP64 iteration to about 1e-5; symmetric swaps amplify a 1e-7 input change to
+O(1) after 10-20 iterations, so the exactly symmetric 4-agent circle is
+compared up to k = 10 only).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_helpers import (gpu_solve, gpu_state, oracle_mats, oracle_solve, planner,
+                               rel_inf)
+
+pytestmark = pytest.mark.gpu
+XI_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("n,m,T,mask", [(4, 50, 5.0, 63), (16, 100, 8.0, 63),
+                                        (5, 13, 2.0, 0b011011), (3, 11, 1.0, 0b001001)])
+def test_kkt_inverse_matches_oracle(n, m, T, mask):
+    prob = W.Problem(n=n, m=m, T=T, start=np.zeros((n, 3), np.float32),
+                     goal=np.zeros((n, 3), np.float32))
+    pl = planner(prob, bc_mask=mask)
+    M = oracle_mats(prob, bc_mask=mask)
+    Kg = pl.kkt_inverse()
+    assert Kg.shape == M.Kinv.shape
+    assert rel_inf(Kg, M.Kinv) < 1e-10
+    assert pl.info.kkt_check < 1e-9
+
+
+@pytest.mark.parametrize("prob", [W.config1(), W.config2(0), W.random_box(7, 3, m=23, T=3.0)],
+                         ids=["circle4", "box16", "box7_m23"])
+def test_initial_state(prob):
+    pl = planner(prob)
+    xi, r, k = gpu_solve(pl, [prob], 0)
+    M = oracle_mats(prob)
+    st = O.init_state(M, O.boundary_values(prob.start, prob.goal))
+    assert k[0] == 0
+    assert rel_inf(xi[0].reshape(3, -1), st.xi) < 1e-5
+    assert abs(r[0] - st.r_max) <= 1e-4 * max(st.r_max, 1e-3)
+
+
+@pytest.mark.parametrize("mode", ["R2", "R3"])
+def test_circle4_within_parity_horizon(mode):
+    prob = W.config1()
+    pl = planner(prob, mode)
+    M = oracle_mats(prob)
+    for k in [1, 2, 5, 10]:
+        xi, r, kk = gpu_solve(pl, [prob], k)
+        st = oracle_solve(M, prob, k, mode=mode)
+        assert kk[0] == k
+        e = rel_inf(xi[0].reshape(3, -1), st.xi)
+        assert e < XI_TOL, (k, e)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_box16_parity_over_iterations(seed):
+    prob = W.config2(seed)
+    pl = planner(prob)
+    M = oracle_mats(prob)
+    for k in [1, 10, 50, 200]:
+        xi, r, kk = gpu_solve(pl, [prob], k)
+        st = oracle_solve(M, prob, k)
+        e = rel_inf(xi[0].reshape(3, -1), st.xi)
+        assert e < XI_TOL, (k, e)
+        assert abs(r[0] - st.r_max) <= 2e-3 * max(st.r_max, 1e-2), (k, r[0], st.r_max)
+
+
+def test_box16_tolerance_stop():
+    prob = W.config2(0)
+    pl = planner(prob)
+    M = oracle_mats(prob)
+    xi, r, k = gpu_solve(pl, [prob], 500, 1e-2)
+    st = oracle_solve(M, prob, 500, 1e-2)
+    assert abs(int(k[0]) - st.k) <= 2, (k[0], st.k)
+    assert r[0] < 1.0e-2 * 1.01
+    if int(k[0]) == st.k:
+        assert rel_inf(xi[0].reshape(3, -1), st.xi) < XI_TOL
+
+
+@pytest.mark.parametrize("n,m,mode", [(5, 30, "R2"), (16, 100, "R2"), (24, 40, "R3"),
+                                      (33, 17, "R2"), (2, 12, "R2")])
+def test_one_iteration_from_warm_state(n, m, mode):
+    """Sub-step parity: from the oracle's own state after 15 iterations, one
+    GPU iteration (projection, QP, alpha/beta, d, lambda) matches the oracle."""
+    prob = W.random_box(n, 40 + n, box=(6.0, 6.0, 3.0), m=m, T=6.0)
+    M = oracle_mats(prob)
+    st15 = oracle_solve(M, prob, 15, mode=mode)
+    xi0 = st15.xi.astype(np.float32)
+    lam0 = st15.lam.astype(np.float32)
+    p = n * (n - 1) // 2
+    ws = O.warm_state(M, xi0.astype(np.float64), lam0.astype(np.float64), mode)
+    ref = O.am_iteration(M, ws, O.boundary_values(prob.start, prob.goal), mode)
+    pl = planner(prob, mode)
+    xi, r, k = gpu_solve(pl, [prob], 1, xi_init=xi0.reshape(1, 3, n, -1),
+                         lambda_init=lam0.reshape(1, 3, p, m))
+    assert k[0] == 1
+    assert rel_inf(xi[0].reshape(3, -1), ref.xi) < XI_TOL
+    lam, al, be, d = gpu_state(pl)
+    assert rel_inf(lam[0].reshape(3, -1), ref.lam) < 1e-4
+    np.testing.assert_allclose(d[0].ravel(), ref.d, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(be[0].ravel(), ref.beta, atol=1e-3)
+    da = np.angle(np.exp(1j * (al[0].ravel() - ref.alpha)))
+    big = np.hypot(*O.pair_differences(M, ref.xi)[:2]) > 1e-3
+    assert np.abs(da[big]).max() < 1e-3
+
+
+def test_batch_matches_single_instances():
+    probs = [W.random_box(16, 100 + i, box=(8.0, 8.0, 4.0)) for i in range(6)]
+    pl = planner(probs[0], max_batch=6)
+    xb, rb, kb = gpu_solve(pl, probs, 20)
+    for i, p in enumerate(probs):
+        x1, r1, k1 = gpu_solve(pl, [p], 20)
+        assert rel_inf(xb[i], x1[0]) < 1e-5
+        assert kb[i] == k1[0] == 20
+
+
+def test_trace_mode_is_bitwise_identical():
+    prob = W.config2(2)
+    pl = planner(prob)
+    xa, ra, ka = gpu_solve(pl, [prob], 30, 1e-3)
+    pl.set_trace(True)
+    xb, rb, kb = gpu_solve(pl, [prob], 30, 1e-3)
+    ms, cnt = pl.stats()
+    assert np.array_equal(xa, xb) and np.array_equal(ra, rb) and np.array_equal(ka, kb)
+    assert cnt[0] == cnt[2] == int(kb[0]) and cnt[1] == int(kb[0]) + 1
+    assert all(t > 0 for t in ms)
+
+
+def test_boundary_values_and_masks():
+    rng = np.random.default_rng(9)
+    prob = W.random_box(3, 9, box=(4.0, 4.0, 2.0), m=30, T=4.0)
+    extra = rng.uniform(-0.5, 0.5, (3, 2, 2, 3)).astype(np.float32)
+    M = oracle_mats(prob)
+    pl = planner(prob)
+    xi, r, k = gpu_solve(pl, [prob], 12, bc_extra=extra[None])
+    st = O.solve(M, prob.start, prob.goal, 12, 0.0, "R2", bc_extra=extra)
+    assert rel_inf(xi[0].reshape(3, -1), st.xi) < XI_TOL
+    beq = O.boundary_values(prob.start, prob.goal, bc_extra=extra)
+    assert np.abs((M.A_eq @ xi[0].reshape(3, -1).astype(np.float64).T).T - beq).max() < 1e-4
+    # positions-only boundary conditions
+    M2 = oracle_mats(prob, bc_mask=0b001001)
+    pl2 = planner(prob, bc_mask=0b001001)
+    xi2, _, _ = gpu_solve(pl2, [prob], 12)
+    st2 = O.solve(M2, prob.start, prob.goal, 12, 0.0, "R2")
+    assert rel_inf(xi2[0].reshape(3, -1), st2.xi) < XI_TOL
+
+
+def test_nonfinite_input_is_flagged():
+    probs = [W.random_box(8, 1), W.random_box(8, 2)]
+    probs[1].start[3, 1] = np.nan
+    pl = planner(probs[0], max_batch=2)
+    xi, r, k = gpu_solve(pl, probs, 5)
+    assert k[1] == -1 and np.isnan(r[1])
+    assert k[0] == 5 and np.isfinite(r[0])
+
+
+def test_shell64_first_iterations():
+    probs = W.config4(2)
+    pl = planner(probs[0], "R3", max_batch=2)
+    M = oracle_mats(probs[0])
+    xi, r, k = gpu_solve(pl, probs, 1)
+    for i, p in enumerate(probs):
+        st = oracle_solve(M, p, 1, mode="R3")
+        assert rel_inf(xi[i].reshape(3, -1), st.xi) < XI_TOL
