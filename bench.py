@@ -1,0 +1,370 @@
+"""Benchmark of the alternating-minimisation iteration on B300.
+
+Default workload: 256 instances of 64 agents each (degree-10 Bernstein
+trajectories, m = 100 samples over T = 8 s, starts on a 5 m sphere shell with
+antipodal goals, lambda-free projection), the batched form on which the
+instance-iterations/s metric is quoted.  One step = one pass of the whole
+iteration (pair projection, multiplier update, A^T reduction, cached KKT
+inverse apply, stopping test) over the batch; the timed region is one
+solve call of K iterations on data already resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amto|reference]
+
+Under torchrun (N > 1) every rank solves its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "instance-iterations/s and p50/p99 solve latency vs plain FP32, same residual"
+UNIT = "instance-iterations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="amto", choices=["amto", "reference"])
+    ap.add_argument("--batch", type=int, default=256, help="instances per GPU")
+    ap.add_argument("--agents", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain per-instance line, cpu baseline and e2e leg")
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    import workloads as W
+    probs = W.config4(args.batch, seed=rank, n=args.agents)
+    return probs
+
+
+def algorithmic_pair_bytes(n, m, batch):
+    """Bytes the pair step must move per launch: lambda read + write (24 B per
+    pair-time) and the trajectories read (12 B per coefficient row)."""
+    pt = m * n * (n - 1) // 2
+    return batch * (24 * pt + 3 * 11 * n * 4)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ["iterate.cu"]:
+        with open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(n, batch):
+    """Per-launch DRAM traffic of the pair kernel from the committed ncu summary,
+    scaled to `batch` instances; None if the kernel changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "pair_kernel_shell64.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    mb = re.search(r"dram_bytes_per_instance_launch:\s*([0-9.eE+]+)", text)
+    mn = re.search(r"agents:\s*(\d+)", text)
+    if not (mh and mb and mn) or mh.group(1) != source_hash() or int(mn.group(1)) != n:
+        return None
+    return float(mb.group(1)) * batch
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons via NVML while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+
+    def __enter__(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            self._nv = None
+            return self
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def _run(self):
+        nv = self._nv
+        names = {
+            "hw_slowdown": getattr(nv, "nvmlClocksThrottleReasonHwSlowdown", 0x8),
+            "sw_thermal_slowdown": getattr(nv, "nvmlClocksThrottleReasonSwThermalSlowdown", 0x20),
+            "hw_thermal_slowdown": getattr(nv, "nvmlClocksThrottleReasonHwThermalSlowdown", 0x40),
+            "sw_power_cap": getattr(nv, "nvmlClocksThrottleReasonSwPowerCap", 0x4),
+        }
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self._h)
+                for k, bit in names.items():
+                    if r & bit:
+                        self.reasons.add(k)
+            except Exception:
+                pass
+            time.sleep(0.05)
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join()
+
+    def summary(self):
+        s = sorted(self.samples)
+        med = s[len(s) // 2] if s else None
+        return {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                "samples": len(s)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def cpu_baseline_oracle(prob, seconds=12.0, mode="R3"):
+    """The FP64 oracle, as it stands, on a bounded sample: one instance of the
+    workload iterated for about `seconds`."""
+    import oracle as O
+    from threadpoolctl import threadpool_info
+    M = O.build_matrices(prob.n, prob.m, prob.degree, prob.T, prob.a, prob.b, prob.rho)
+    beq = O.boundary_values(prob.start, prob.goal)
+    st = O.init_state(M, beq, mode)
+    t0 = time.perf_counter()
+    its = 0
+    while time.perf_counter() - t0 < seconds:
+        st = O.am_iteration(M, st, beq, mode)
+        its += 1
+    dt = time.perf_counter() - t0
+    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    return {"value": its / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"1 instance of {prob.n} agents (m={prob.m}), {its} iterations in "
+                      f"{dt:.1f} s, FP64 numpy/scipy"}
+
+
+def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
+    """Plain FP32 per-instance GPU solve: 16 agents, 6x6x3 m box, m = 100,
+    iterate to max residual < 1e-2 or 500 iterations, one instance at a time."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Planner
+    pl = Planner(16, 100, 8.0, max_batch=1)
+    lat, its, res = [], [], []
+    for rep in range(2):
+        for sd in seeds:
+            p = W.config2(sd)
+            s = torch.from_numpy(p.start[None]).cuda()
+            g = torch.from_numpy(p.goal[None]).cuda()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            xi, r, k = pl.solve(s, g, 500, 1e-2)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep == 1:
+                lat.append(e0.elapsed_time(e1))
+                its.append(int(k.item()))
+                res.append(float(r.item()))
+    pl.close()
+    lat = np.array(lat)
+    return {"workload": "16 agents, 6x6x3 m box, m=100, tol 1e-2 / 500 iterations, batch 1",
+            "value": float(sum(its) / (lat.sum() / 1e3)), "unit": UNIT,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "iterations": its, "final_resid_max": max(res)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle as O
+    from threadpoolctl import threadpool_info
+    probs = workload(args, 0)[:4]
+    M = O.build_matrices(probs[0].n, probs[0].m, probs[0].degree, probs[0].T, probs[0].a,
+                         probs[0].b, probs[0].rho)
+    states = []
+    for p in probs:
+        beq = O.boundary_values(p.start, p.goal)
+        states.append([beq, O.init_state(M, beq, "R3")])
+    for w in range(args.warmup):
+        beq, st = states[w % len(states)]
+        states[w % len(states)][1] = O.am_iteration(M, st, beq, "R3")
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        beq, st = states[k % len(states)]
+        states[k % len(states)][1] = O.am_iteration(M, st, beq, "R3")
+    dt = time.perf_counter() - t0
+    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    value = args.steps / dt
+    sample = (f"{args.steps} oracle iterations cycling over {len(probs)} instances of "
+              f"{probs[0].n} agents (one instance-iteration per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.batch} x {args.agents}-agent sphere-shell swap, "
+                                   "degree 10, m=100, T=8 s, lambda-free projection",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads as W
+    from paper_2011_04240_b300 import Planner, amto
+
+    probs = workload(args, rank)
+    n, m, B, K = probs[0].n, probs[0].m, len(probs), args.steps
+    pl = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
+                 proj_mode=amto.PROJ_NOLAMBDA, max_batch=B)
+    s_np, g_np = W.stack(probs)
+    s = torch.from_numpy(s_np).cuda()
+    g = torch.from_numpy(g_np).cuda()
+    out = (torch.empty((B, 3, n, 11), device="cuda"), torch.empty((B,), device="cuda"),
+           torch.empty((B,), device="cuda", dtype=torch.int32))
+    # warm-up: W iterations (also instantiates the solve graph)
+    pl.solve(s, g, max(args.warmup, 3), out=out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        pl.solve(s, g, K, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    iters_done = int(out[2].sum().item())
+    assert iters_done == B * K, (iters_done, B * K)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * B * K / (ms_max / 1e3)
+
+    extras = {}
+    if not args.no_extras:
+        # e2e through the public API: pinned host inputs -> device, solve, results -> host
+        hs = torch.from_numpy(s_np).pin_memory()
+        hg = torch.from_numpy(g_np).pin_memory()
+        hx = torch.empty((B, 3, n, 11)).pin_memory()
+        hr = torch.empty((B,)).pin_memory()
+        hk = torch.empty((B,), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        f0.record(stream)
+        s.copy_(hs, non_blocking=True)
+        g.copy_(hg, non_blocking=True)
+        pl.solve(s, g, K, out=out)
+        hx.copy_(out[0], non_blocking=True)
+        hr.copy_(out[1], non_blocking=True)
+        hk.copy_(out[2], non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        e2e_t = torch.tensor([e2e_ms], device="cuda")
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        h2d = (hs.numel() + hg.numel()) * 4
+        d2h = hx.numel() * 4 + hr.numel() * 4 + hk.numel() * 4
+        extras["e2e"] = {"value": world * B * K / (float(e2e_t.item()) / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                         "note": "one solve of K iterations per timed call; bytes per solve / K"}
+        # per-kernel device time from an event-traced pass of the same solve
+        pl.set_trace(True)
+        pl.solve(s, g, K, out=out)
+        torch.cuda.synchronize()
+        kms, kcnt = pl.stats()
+        pl.set_trace(False)
+        pair_ms = kms[0] / max(kcnt[0], 1)
+        hbm, src = peaks()
+        alg = algorithmic_pair_bytes(n, m, B)
+        achieved = alg / (pair_ms / 1e3) / 1e9
+        extras["roofline"] = {"bound": "hbm", "kernel": "k_pair (fused pair step)",
+                              "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                              "frac": achieved / hbm, "peak_source": src,
+                              "traffic": profile_traffic(n, B),
+                              "algorithmic_bytes_per_launch": alg,
+                              "avg_launch_ms": pair_ms,
+                              "kernel_ms_per_iteration": {"pair": pair_ms,
+                                                          "rhs": kms[1] / max(kcnt[1], 1),
+                                                          "apply": kms[2] / max(kcnt[2], 1)}}
+        if rank == 0:
+            extras["plain_fp32_per_instance"] = plain_per_instance()
+            extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{B} x {n}-agent sphere-shell antipodal swap per GPU, "
+                                       "degree-10 Bernstein, m=100, T=8 s, a=0.6, b=1.2, rho=1, "
+                                       "lambda-free projection, fixed iterations",
+                           "batch_per_gpu": B, "agents": n, "m": m,
+                           "l2": "inputs larger than L2 (multiplier state "
+                                 f"{2 * pl.info.lambda_floats * 4 * B / 1e9:.2f} GB)",
+                           "parallelism": f"replicas x{world}"},
+                "clocks": clk.summary(),
+                "gpu_launches": 3 * (K + 1) + 4}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    pl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

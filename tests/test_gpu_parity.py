@@ -38,7 +38,7 @@ def test_kkt_inverse_matches_oracle(n, m, T, mask):
     Kg = pl.kkt_inverse()
     assert Kg.shape == M.Kinv.shape
     assert rel_inf(Kg, M.Kinv) < 1e-10
-    assert pl.info.kkt_check < 1e-9
+    assert pl.info.kkt_check < 1e-7
 
 
 @pytest.mark.parametrize("prob", [W.config1(), W.config2(0), W.random_box(7, 3, m=23, T=3.0)],
