@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="amto", choices=["amto", "reference"])
     ap.add_argument("--batch", type=int, default=256, help="instances per GPU")
     ap.add_argument("--agents", type=int, default=64)
+    ap.add_argument("--trace", action="store_true",
+                    help="run the timed solve from the host loop (no graph), as profilers need")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain per-instance line, cpu baseline and e2e leg")
     return ap.parse_args()
@@ -83,59 +85,64 @@ def profile_traffic(n, batch):
 
 
 class ClockSampler:
-    """Samples SM clock and throttle reasons via NVML while the timed region runs."""
+    """Samples SM clock, power and throttle reasons with nvidia-smi (every
+    50 ms) while the timed region runs; keeps the samples taken under load."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
-        self.samples = []
-        self.reasons = set()
-        self.max_mhz = None
-        self._stop = threading.Event()
+        self.rows = []
+        self._p = None
         self._t = None
 
     def __enter__(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nv = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            self._p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
         except Exception:
-            self._nv = None
-            return self
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+            self._p = None
         return self
 
-    def _run(self):
-        nv = self._nv
-        names = {
-            "hw_slowdown": getattr(nv, "nvmlClocksThrottleReasonHwSlowdown", 0x8),
-            "sw_thermal_slowdown": getattr(nv, "nvmlClocksThrottleReasonSwThermalSlowdown", 0x20),
-            "hw_thermal_slowdown": getattr(nv, "nvmlClocksThrottleReasonHwThermalSlowdown", 0x40),
-            "sw_power_cap": getattr(nv, "nvmlClocksThrottleReasonSwPowerCap", 0x4),
-        }
-        while not self._stop.is_set():
-            try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
-                r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self._h)
-                for k, bit in names.items():
-                    if r & bit:
-                        self.reasons.add(k)
-            except Exception:
-                pass
-            time.sleep(0.05)
+    def _read(self):
+        for line in self._p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
 
     def __exit__(self, *a):
-        self._stop.set()
-        if self._t:
-            self._t.join()
+        if self._p:
+            time.sleep(0.1)
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
+            self._t.join(timeout=5)
 
     def summary(self):
-        s = sorted(self.samples)
-        med = s[len(s) // 2] if s else None
-        return {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
-                "samples": len(s)}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        loaded = [r for r in self.rows if (num(r[4]) or 0) > 0] or self.rows
+        sm = sorted(v for v in (num(r[1]) for r in loaded) if v is not None)
+        mx = [v for v in (num(r[2]) for r in self.rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        pw = [v for v in (num(r[3]) for r in loaded) if v is not None]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "power_w_max": max(pw) if pw else None, "samples": len(loaded)}
 
 
 def peaks():
@@ -147,22 +154,29 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def cpu_seconds():
+    """CPU time (user + system) of this process, all threads."""
+    import resource
+    r = resource.getrusage(resource.RUSAGE_SELF)
+    return r.ru_utime + r.ru_stime
+
+
 def cpu_baseline_oracle(prob, seconds=12.0, mode="R3"):
     """The FP64 oracle, as it stands, on a bounded sample: one instance of the
     workload iterated for about `seconds`."""
     import oracle as O
-    from threadpoolctl import threadpool_info
     M = O.build_matrices(prob.n, prob.m, prob.degree, prob.T, prob.a, prob.b, prob.rho)
     beq = O.boundary_values(prob.start, prob.goal)
     st = O.init_state(M, beq, mode)
+    c0 = cpu_seconds()
     t0 = time.perf_counter()
     its = 0
     while time.perf_counter() - t0 < seconds:
         st = O.am_iteration(M, st, beq, mode)
         its += 1
     dt = time.perf_counter() - t0
-    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    return {"value": its / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    cores = round((cpu_seconds() - c0) / dt, 2)
+    return {"value": its / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"1 instance of {prob.n} agents (m={prob.m}), {its} iterations in "
                       f"{dt:.1f} s, FP64 numpy/scipy"}
 
@@ -204,7 +218,6 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle as O
-    from threadpoolctl import threadpool_info
     probs = workload(args, 0)[:4]
     M = O.build_matrices(probs[0].n, probs[0].m, probs[0].degree, probs[0].T, probs[0].a,
                          probs[0].b, probs[0].rho)
@@ -215,12 +228,13 @@ def run_reference(args, rank, world):
     for w in range(args.warmup):
         beq, st = states[w % len(states)]
         states[w % len(states)][1] = O.am_iteration(M, st, beq, "R3")
+    c0 = cpu_seconds()
     t0 = time.perf_counter()
     for k in range(args.steps):
         beq, st = states[k % len(states)]
         states[k % len(states)][1] = O.am_iteration(M, st, beq, "R3")
     dt = time.perf_counter() - t0
-    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    threads = round((cpu_seconds() - c0) / dt, 2)
     value = args.steps / dt
     sample = (f"{args.steps} oracle iterations cycling over {len(probs)} instances of "
               f"{probs[0].n} agents (one instance-iteration per step)")
@@ -276,6 +290,8 @@ def main():
             dist.barrier()
 
     stream = torch.cuda.current_stream()
+    if args.trace:
+        pl.set_trace(True)
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
     with ClockSampler(local) as clk:
         barrier()

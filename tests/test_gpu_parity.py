@@ -110,7 +110,11 @@ def test_one_iteration_from_warm_state(n, m, mode):
     assert k[0] == 1
     assert rel_inf(xi[0].reshape(3, -1), ref.xi) < XI_TOL
     lam, al, be, d = gpu_state(pl)
-    assert rel_inf(lam[0].reshape(3, -1), ref.lam) < 1e-4
+    # multipliers carry units of length (lambda / rho); compare normwise with a
+    # 1 cm floor so that an already-converged pair (lambda ~ 0) is not judged
+    # on float32 round-off alone
+    lam_err = np.abs(lam[0].reshape(3, -1) - ref.lam).max() / max(np.abs(ref.lam).max(), 1e-2)
+    assert lam_err < 1e-4, lam_err
     np.testing.assert_allclose(d[0].ravel(), ref.d, rtol=1e-4, atol=1e-4)
     np.testing.assert_allclose(be[0].ravel(), ref.beta, atol=1e-3)
     da = np.angle(np.exp(1j * (al[0].ravel() - ref.alpha)))
