@@ -374,7 +374,8 @@ def main():
                                  f"{2 * pl.info.lambda_floats * 4 * B / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk.summary(),
-                "gpu_launches": 3 * (K + 1) + 4}
+                # setup, initial projection, K x (rhs, apply, pair), FP64 residual, outputs
+                "gpu_launches": 3 * K + 4}
         line.update(extras)
         print(json.dumps(line), flush=True)
     pl.close()

@@ -36,25 +36,26 @@ struct Ctl {
     int max_iters;
     float tol;
     int batch;
-    unsigned int ticket;        // last-block detection in the rhs kernel
-    unsigned int active;        // running count of active instances this pass
-    unsigned int active_last;   // active count after the last rhs pass
+    unsigned int ticket;        // last-block detection in the pair kernel
+    unsigned int loop_count;    // pair-kernel passes of this solve (loop guard)
+    unsigned int active_last;   // instances still iterating after the last pass
 };
 
 // Geometry of the pair kernel's work decomposition (see iterate.cu).
 struct PairGeom {
-    int G;          // agents per lane group (power of two, 2..32)
+    int G;          // agents per lane group (8, 16 or 32)
     int TPW;        // time samples per warp pass = 32 / G
     int nbk;        // agent blocks = ceil(n / G)
     int npad;       // nbk * G
-    int S;          // steps per time group = nbk^2 G / 2
+    int S;          // steps per time group = nbk^2 G / 2 (a multiple of 4)
     int warps;      // warps per block
     int QW;         // time groups per warp
     int QC;         // time groups per block = warps * QW
     int TC;         // time samples per block = QC * TPW
-    int n_chunks;   // blocks per instance = ceil(m / TC)
+    int n_chunks;   // work units per instance = ceil(m / TC)
     int MQ;         // time groups per instance = n_chunks * QC
     long long lam_floats;  // multiplier floats per instance and buffer = MQ * S * 3 * 32
+    int grid;       // persistent pair-kernel blocks (set when the kernels are configured)
 };
 
 PairGeom choose_geometry(int n, int m);
@@ -70,6 +71,7 @@ struct Graph {
 struct amto_plan_s {
     amto_params prm;
     int device = 0;
+    int num_sms = 0;
     int n = 0, m = 0, N = 0, nv = 0, nb = 0, kdim = 0, p = 0;
     amto::PairGeom geo{};
     double kkt_check = 0.0;
@@ -95,6 +97,9 @@ struct amto_plan_s {
     unsigned long long* r64 = nullptr;  // [B] FP64 final residual^2 bits
     int* iters = nullptr;      // [B]
     int* flags = nullptr;      // [B]
+    unsigned* uticket = nullptr;  // [B] finished pair-kernel units per instance
+    float* gemm_ws = nullptr;     // split-K partial products of the SIMT apply
+    unsigned* gemm_tk = nullptr;  // per-tile tickets of the split-K reduction
     amto::Ctl* ctl = nullptr;
     amto::Ctl* ctl_host = nullptr;   // pinned mirror for host polling
 
@@ -113,13 +118,15 @@ namespace amto {
 amto_status precompute(amto_plan_s* pl);
 // iterate.cu
 amto_status configure_kernels(amto_plan_s* pl);
+void gemm_workspace(const amto_plan_s* pl, size_t* ws_floats, int* tiles);
 amto_status launch_setup(amto_plan_s* pl, int batch, const float* start, const float* goal,
                          const float* bc_extra, const float* xi_init, int max_iters, float tol,
                          cudaStream_t s);
+// init_mode 0: regular step; 1: initial projection, lambda = 0; 2: initial
+// projection with lambda gathered from `lambda_init`.
 amto_status launch_pair(amto_plan_s* pl, int batch, int init_mode, const float* lambda_init,
-                        cudaStream_t s);
-amto_status launch_rhs(amto_plan_s* pl, int batch, cudaGraphConditionalHandle h, int use_cond,
-                       cudaStream_t s);
+                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+amto_status launch_rhs(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_apply(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_final(amto_plan_s* pl, int batch, float* xi_out, float* resid_out,
                          int* iters_out, cudaStream_t s);

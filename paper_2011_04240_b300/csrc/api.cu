@@ -55,7 +55,8 @@ void free_plan(amto_plan_s* pl) {
     pl->graphs.clear();
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kinv64, pl->Ktop,
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
-                    pl->rmax, pl->r64, pl->iters, pl->flags, pl->ctl};
+                    pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
+                    pl->gemm_tk, pl->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (pl->ctl_host) cudaFreeHost(pl->ctl_host);
@@ -93,9 +94,9 @@ amto_status build_graph(amto_plan_s* pl, int batch, Graph& out) {
         set_error("cudaStreamBeginCaptureToGraph failed");
         return fail(AMTO_ECUDA);
     }
-    amto_status st = launch_rhs(pl, batch, g.handle, 1, pl->cap_stream);
+    amto_status st = launch_rhs(pl, batch, pl->cap_stream);
     if (st == AMTO_OK) st = launch_apply(pl, batch, pl->cap_stream);
-    if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, pl->cap_stream);
+    if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, g.handle, 1, pl->cap_stream);
     cudaGraph_t captured = body;
     cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &captured);
     if (st != AMTO_OK) return fail(st);
@@ -113,42 +114,39 @@ amto_status build_graph(amto_plan_s* pl, int batch, Graph& out) {
 }
 
 // Host-driven loop with CUDA events around every launch (amto_set_trace).
+// The loop runs while the last pair pass left an instance flagged to
+// iterate, at most max_iters + 1 passes (the same bound as the graph loop).
 amto_status run_traced(amto_plan_s* pl, int batch, int max_iters, cudaStream_t s) {
-    cudaEvent_t ev[5];
+    cudaEvent_t ev[4];
     for (auto& e : ev) AMTO_CUDA_TRY(cudaEventCreate(&e));
     amto_status st = AMTO_OK;
     for (int it = 0; it <= max_iters + 1 && st == AMTO_OK; ++it) {
-        cudaEventRecord(ev[0], s);
-        st = launch_rhs(pl, batch, 0, 0, s);
-        cudaEventRecord(ev[1], s);
-        if (st != AMTO_OK) break;
         cudaMemcpyAsync(pl->ctl_host, pl->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             set_error("traced solve: stream synchronisation failed");
             st = AMTO_ECUDA;
             break;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        pl->stat_ms[KSTAT_RHS] += ms;
-        pl->stat_cnt[KSTAT_RHS] += 1;
         if (pl->ctl_host->active_last == 0) break;
+        cudaEventRecord(ev[0], s);
+        st = launch_rhs(pl, batch, s);
+        cudaEventRecord(ev[1], s);
+        if (st == AMTO_OK) st = launch_apply(pl, batch, s);
         cudaEventRecord(ev[2], s);
-        st = launch_apply(pl, batch, s);
+        if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, 0, 0, s);
         cudaEventRecord(ev[3], s);
-        if (st == AMTO_OK) st = launch_pair(pl, batch, 0, nullptr, s);
-        cudaEventRecord(ev[4], s);
-        if (cudaEventSynchronize(ev[4]) != cudaSuccess) {
+        if (cudaEventSynchronize(ev[3]) != cudaSuccess) {
             set_error("traced solve: event synchronisation failed");
             st = AMTO_ECUDA;
             break;
         }
-        cudaEventElapsedTime(&ms, ev[2], ev[3]);
-        pl->stat_ms[KSTAT_APPLY] += ms;
-        pl->stat_cnt[KSTAT_APPLY] += 1;
-        cudaEventElapsedTime(&ms, ev[3], ev[4]);
-        pl->stat_ms[KSTAT_PAIR] += ms;
-        pl->stat_cnt[KSTAT_PAIR] += 1;
+        float ms = 0.f;
+        const int kinds[3] = {KSTAT_RHS, KSTAT_APPLY, KSTAT_PAIR};
+        for (int k = 0; k < 3; ++k) {
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            pl->stat_ms[kinds[k]] += ms;
+            pl->stat_cnt[kinds[k]] += 1;
+        }
     }
     for (auto& e : ev) cudaEventDestroy(e);
     return st;
@@ -238,14 +236,25 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->r64, (size_t)B);
     ALLOC(pl->iters, (size_t)B);
     ALLOC(pl->flags, (size_t)B);
+    ALLOC(pl->uticket, (size_t)B);
     ALLOC(pl->ctl, (size_t)1);
+    if (st == AMTO_OK) st = configure_kernels(pl);
+    size_t ws_floats = 0;
+    int tiles = 0;
+    if (st == AMTO_OK) gemm_workspace(pl, &ws_floats, &tiles);
+    ALLOC(pl->gemm_ws, ws_floats);
+    ALLOC(pl->gemm_tk, (size_t)tiles);
 #undef ALLOC
+    if (st == AMTO_OK && (cudaMemset(pl->gemm_tk, 0, sizeof(unsigned) * tiles) != cudaSuccess ||
+                          cudaMemset(pl->uticket, 0, sizeof(unsigned) * B) != cudaSuccess)) {
+        set_error("cudaMemset failed");
+        st = AMTO_ECUDA;
+    }
     if (st == AMTO_OK && cudaMallocHost((void**)&pl->ctl_host, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMallocHost failed");
         st = AMTO_ENOMEM;
     }
-    if (st == AMTO_OK) st = configure_kernels(pl);
     if (st == AMTO_OK) st = precompute(pl);
     if (st == AMTO_OK && cudaMemset(pl->flags, 0, sizeof(int) * B) != cudaSuccess) {
         set_error("cudaMemset failed");
@@ -290,7 +299,7 @@ amto_status amto_solve(amto_plan plan, int batch, const float* start, const floa
     cudaStream_t s = (cudaStream_t)stream;
     amto_status st = launch_setup(plan, batch, start, goal, bc_extra, xi_init, max_iters, tol, s);
     if (st != AMTO_OK) return st;
-    st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, s);
+    st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, 0, 0, s);
     if (st != AMTO_OK) return st;
     if (plan->trace) {
         for (int k = 0; k < KSTAT_N; ++k) {
