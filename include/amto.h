@@ -156,6 +156,39 @@ amto_status amto_solve(amto_plan plan, int batch,
                        void* stream);
 
 /*
+ * amto_solve_static - the solve of amto_solve for ONE instance (batch 1, no
+ * boundary extras, no warm start) that allocates no memory at all.  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * For callers that cannot call cudaMalloc while they plan: a control loop
+ * with a fixed memory budget, a process whose device heap is owned by its
+ * own pool allocator, or a thread that must not take the allocator's locks.
+ * All per-solve buffers (trajectories, boundary values, both multiplier
+ * buffers, partial sums, right-hand side, flags) come from one static device
+ * array of 8 MiB that every GPU loading this library holds until the
+ * process exits.  The plan's read-only constants, made by amto_create, are
+ * reused.  A plan whose one-instance buffers do not fit in 8 MiB (about
+ * n > 80 agents at m = 100) is rejected with AMTO_EINVAL and a message
+ * giving the bytes it would need.
+ *
+ *   start, goal  device [1][n][3] float32;  xi_out device [1][3][n][N+1];
+ *   resid_out, iters_out as in amto_solve (device, may be NULL).
+ *
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture on the device.  Every call shares the one array
+ * and overwrites it; the flags and counters that must start at zero are
+ * cleared by each call.  Calls that overlap on the GPU (for example on two
+ * streams) race on the array: serialise them.  The loop is driven from the
+ * host, which synchronises `stream` every 8 iterations to read the stop
+ * flag.  Results are the same as amto_solve on the same plan and inputs.
+ * Errors: EINVAL, ECUDA.
+ */
+amto_status amto_solve_static(amto_plan plan, const float* start, const float* goal,
+                              int max_iters, float tol, float* xi_out, float* resid_out,
+                              int* iters_out, void* stream);
+
+/*
  * amto_get_state - read back the multipliers of the last solve on this plan
  * and alpha, beta, d of its last projection (Eqs. sphere_project, step_d).
  * All outputs are device pointers, each may be NULL:

@@ -54,6 +54,8 @@ SIGNATURES = {
     "amto_destroy": (None, [_P]),
     "amto_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int,
                                   ctypes.c_float, _P, _P, _P, _P]),
+    "amto_solve_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_float, _P, _P, _P,
+                                         _P]),
     "amto_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "amto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "amto_get_kkt_inverse": (ctypes.c_int, [_P, _P]),
@@ -116,6 +118,14 @@ def solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init, max_iters, t
           xi_out, resid_out, iters_out, stream) -> None:
     _check(load().amto_solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init,
                              max_iters, tol, xi_out, resid_out, iters_out, stream))
+
+
+def solve_static(plan, start, goal, max_iters, tol, xi_out, resid_out, iters_out,
+                 stream) -> None:
+    """One-instance solve whose scratch lives in the library's static device
+    array (no allocation; see include/amto.h)."""
+    _check(load().amto_solve_static(plan, start, goal, max_iters, tol, xi_out, resid_out,
+                                    iters_out, stream))
 
 
 def get_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, stream) -> None:
