@@ -39,6 +39,7 @@ struct Ctl {
     unsigned int ticket;        // last-block detection in the pair kernel
     unsigned int loop_count;    // pair-kernel passes of this solve (loop guard)
     unsigned int active_last;   // instances still iterating after the last pass
+    unsigned int error;         // nonzero: a bounded device wait ran out
 };
 
 // Geometry of the pair kernel's work decomposition (see iterate.cu).
