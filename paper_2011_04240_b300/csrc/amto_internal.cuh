@@ -1,6 +1,7 @@
 // Internal declarations of the amto library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -86,6 +87,10 @@ struct amto_plan_s {
     float* E0 = nullptr;       // [nv][nb]  top-right block of the agent-level inverse
     double* Kinv64 = nullptr;  // [kdim][kdim]
     float* Ktop = nullptr;     // [n nv][kdim]
+    int kp = 0;                // padded row length (multiple of 4) of the tensor-core operands
+    float* Kt_hi = nullptr;    // [n nv][kp] TF32-rounded K^-1_top (tensor-core modes)
+    float* Kt_lo = nullptr;    // [n nv][kp] float32 residual K^-1_top - Kt_hi
+    CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;  // TMA descriptors (64-byte aligned type)
 
     // state for max_batch instances (device)
     float* xi = nullptr;       // [B][3][n nv]
@@ -93,7 +98,8 @@ struct amto_plan_s {
     float* lam[2] = {nullptr, nullptr};  // [B][lam_floats]
     float* gpart = nullptr;    // [B][n_chunks][3][n nv]
     float* rpart = nullptr;    // [B][n_chunks]
-    float* rhs = nullptr;      // [B][3][kdim]
+    float* rhs = nullptr;      // [B][3][kp] (TF32-rounded in tensor-core modes)
+    float* rhs_lo = nullptr;   // [B][3][kp] residual rhs - rhs (TF32X3 mode)
     float* rmax = nullptr;     // [B]
     unsigned long long* r64 = nullptr;  // [B] FP64 final residual^2 bits
     int* iters = nullptr;      // [B]
@@ -129,6 +135,10 @@ amto_status launch_pair(amto_plan_s* pl, int batch, int init_mode, const float* 
                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 amto_status launch_rhs(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_apply(amto_plan_s* pl, int batch, cudaStream_t s);
+// apply_tc.cu (tensor-core apply)
+size_t tc_smem_bytes();
+amto_status tc_configure(amto_plan_s* pl);
+amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_final(amto_plan_s* pl, int batch, float* xi_out, float* resid_out,
                          int* iters_out, cudaStream_t s);
 amto_status launch_state(amto_plan_s* pl, int batch, float* lambda_out, float* alpha_out,

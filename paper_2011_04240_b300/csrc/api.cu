@@ -56,6 +56,7 @@ void free_plan(amto_plan_s* pl) {
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kinv64, pl->Ktop,
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
+                    pl->Kt_hi, pl->Kt_lo, pl->rhs_lo,
                     pl->gemm_tk, pl->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -183,8 +184,9 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     if (nb >= p.poly_degree + 1) return einval("more boundary conditions than coefficients");
     if (p.proj_mode != AMTO_PROJ_LITERAL && p.proj_mode != AMTO_PROJ_NOLAMBDA)
         return einval("proj_mode");
-    if (p.precision != AMTO_PREC_FP32)
-        return einval("precision: only AMTO_PREC_FP32 is available in this build");
+    if (p.precision != AMTO_PREC_FP32 && p.precision != AMTO_PREC_TF32X3 &&
+        p.precision != AMTO_PREC_TF32)
+        return einval("precision: AMTO_PREC_FP32, AMTO_PREC_TF32X3 and AMTO_PREC_TF32 are available");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
 
     amto_plan_s* pl = new (std::nothrow) amto_plan_s();
@@ -207,6 +209,8 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m);
+    pl->kp = (pl->kdim + 3) / 4 * 4;  // 16-byte rows for the tensor-memory-access descriptors
+    const bool tc = p.precision == AMTO_PREC_TF32X3 || p.precision == AMTO_PREC_TF32;
     const int B = p.max_batch, n = pl->n, nv = pl->nv, kdim = pl->kdim;
     const size_t nvn = (size_t)n * nv;
 
@@ -225,13 +229,18 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->E0, (size_t)nv * nb);
     ALLOC(pl->Kinv64, (size_t)kdim * kdim);
     ALLOC(pl->Ktop, nvn * kdim);
+    if (tc) {
+        ALLOC(pl->Kt_hi, nvn * pl->kp);
+        ALLOC(pl->Kt_lo, nvn * pl->kp);
+        ALLOC(pl->rhs_lo, (size_t)B * 3 * pl->kp);
+    }
     ALLOC(pl->xi, (size_t)B * 3 * nvn);
     ALLOC(pl->beq, (size_t)B * 3 * n * nb);
     ALLOC(pl->lam[0], (size_t)B * pl->geo.lam_floats);
     ALLOC(pl->lam[1], (size_t)B * pl->geo.lam_floats);
     ALLOC(pl->gpart, (size_t)B * pl->geo.n_chunks * 3 * nvn);
     ALLOC(pl->rpart, (size_t)B * pl->geo.n_chunks);
-    ALLOC(pl->rhs, (size_t)B * 3 * kdim);
+    ALLOC(pl->rhs, (size_t)B * 3 * pl->kp);
     ALLOC(pl->rmax, (size_t)B);
     ALLOC(pl->r64, (size_t)B);
     ALLOC(pl->iters, (size_t)B);
@@ -256,6 +265,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
         st = AMTO_ENOMEM;
     }
     if (st == AMTO_OK) st = precompute(pl);
+    if (st == AMTO_OK && tc) st = tc_configure(pl);
     if (st == AMTO_OK && cudaMemset(pl->flags, 0, sizeof(int) * B) != cudaSuccess) {
         set_error("cudaMemset failed");
         st = AMTO_ECUDA;

@@ -210,6 +210,26 @@ __global__ void k_to_f32(long long count, const double* src, float* dst) {
     if (idx < count) dst[idx] = (float)src[idx];
 }
 
+// Round a float32 to TF32 (10 explicit mantissa bits), to nearest, ties to even.
+__device__ __forceinline__ float tf32_round(float x) {
+    unsigned u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u += 0xfffu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xffffe000u);
+}
+
+// Split the top rows of K^-1 for the tensor-core apply: hi = TF32(K^-1),
+// lo = float32(K^-1 - hi), rows padded to ld columns.
+__global__ void k_split_top(int rows, int kdim, int ld, const double* Kinv, float* hi, float* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)rows * ld) return;
+    int r = (int)(idx / ld), c = (int)(idx % ld);
+    double x = (c < kdim) ? Kinv[(long long)r * kdim + c] : 0.0;
+    float h = tf32_round((float)x);
+    hi[idx] = h;
+    lo[idx] = (float)(x - (double)h);
+}
+
 // E0 = rows [0, nv) and columns [nv, nv+nb) of the agent-level inverse.
 __global__ void k_extract_e0(int nv, int nb, const double* K0inv, float* E0) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -318,6 +338,9 @@ amto_status precompute(amto_plan_s* pl) {
         // top n*nv rows of the row-major inverse are its first rows*kdim entries
         k_to_f32<<<blocks((long long)rows * kdim, 256), 256, 0, s>>>((long long)rows * kdim,
                                                                      pl->Kinv64, pl->Ktop);
+        if (pl->Kt_hi)
+            k_split_top<<<blocks((long long)rows * pl->kp, 256), 256, 0, s>>>(
+                rows, kdim, pl->kp, pl->Kinv64, pl->Kt_hi, pl->Kt_lo);
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);

@@ -72,6 +72,10 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
         set_error("invalid argument: plan is NULL");
         return AMTO_EINVAL;
     }
+    if (plan->prm.precision != AMTO_PREC_FP32) {
+        set_error("invalid argument: amto_solve_static takes plans made with AMTO_PREC_FP32");
+        return AMTO_EINVAL;
+    }
     if (!start || !goal || !xi_out) {
         set_error("invalid argument: start, goal and xi_out are required");
         return AMTO_EINVAL;
@@ -95,7 +99,7 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     const size_t o_lam1 = take(sizeof(float) * (size_t)pl.geo.lam_floats);
     const size_t o_gpart = take(sizeof(float) * NC * 3 * nvn);
     const size_t o_rpart = take(sizeof(float) * NC);
-    const size_t o_rhs = take(sizeof(float) * 3 * (size_t)pl.kdim);
+    const size_t o_rhs = take(sizeof(float) * 3 * (size_t)pl.kp);
     const size_t o_rmax = take(sizeof(float));
     const size_t o_r64 = take(sizeof(unsigned long long));
     const size_t o_iters = take(sizeof(int));
@@ -132,7 +136,7 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     v.n = pl.n; v.m = pl.m; v.N = pl.N; v.nv = pl.nv; v.nb = pl.nb; v.kdim = pl.kdim; v.p = pl.p;
     v.geo = pl.geo;
     v.P32 = pl.P32; v.P64 = pl.P64; v.Q32 = pl.Q32; v.A32 = pl.A32; v.E0 = pl.E0;
-    v.Kinv64 = pl.Kinv64; v.Ktop = pl.Ktop;
+    v.Kinv64 = pl.Kinv64; v.Ktop = pl.Ktop; v.kp = pl.kp;
     v.xi = reinterpret_cast<float*>(base + o_xi);
     v.beq = reinterpret_cast<float*>(base + o_beq);
     v.lam[0] = reinterpret_cast<float*>(base + o_lam0);

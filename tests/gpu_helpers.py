@@ -18,10 +18,14 @@ def rel_inf(a, b) -> float:
     return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
 
 
-def planner(prob: W.Problem, mode="R2", max_batch=1, bc_mask=63):
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4}
+
+
+def planner(prob: W.Problem, mode="R2", max_batch=1, bc_mask=63, precision="fp32"):
     from paper_2011_04240_b300 import Planner
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree,
-                   bc_mask=bc_mask, proj_mode=MODES[mode], max_batch=max_batch)
+                   bc_mask=bc_mask, proj_mode=MODES[mode], max_batch=max_batch,
+                   precision=PRECISIONS[precision])
 
 
 def to_dev(x, dev):

@@ -1,0 +1,66 @@
+"""Parity of the tensor-core (tcgen05, TF32) cached-inverse apply.
+
+The apply xi += K^-1_top [g ; e] (Eq. kkt_step_x) runs as one batched GEMM
+on the tensor cores with float32 accumulation.  With the hi/lo split
+(AMTO_PREC_TF32X3: hi*hi + hi*lo + lo*hi) it must track the float32 SIMT
+path and the FP64 oracle within the float32 tolerance; plain TF32 (one
+product) is accepted on residual only (SURVEY's precision contract).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_helpers import gpu_solve, oracle_mats, oracle_solve, planner, rel_inf
+
+pytestmark = pytest.mark.gpu
+XI_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def test_tf32x3_shell64_matches_oracle_and_fp32():
+    probs = W.config4(8)
+    M = oracle_mats(probs[0])
+    pt = planner(probs[0], "R3", max_batch=8, precision="tf32x3")
+    pf = planner(probs[0], "R3", max_batch=8, precision="fp32")
+    xt, rt, kt = gpu_solve(pt, probs, 1)
+    for i, p in enumerate(probs[:3]):
+        st = oracle_solve(M, p, 1, mode="R3")
+        assert rel_inf(xt[i].reshape(3, -1), st.xi) < XI_TOL
+    xt, rt, kt = gpu_solve(pt, probs, 5)
+    xf, rf, kf = gpu_solve(pf, probs, 5)
+    assert rel_inf(xt, xf) < 2e-5
+    assert np.all(kt == 5)
+
+
+@pytest.mark.parametrize("n,m,B", [(5, 30, 3), (16, 100, 64), (24, 40, 50)])
+def test_tf32x3_partial_tiles_split_k_and_padding(n, m, B):
+    """n = 5: kdim = 85 padded to 88, one 55-row tile; n = 16, B = 64: two
+    row tiles, two column tiles, split over K; n = 24: uneven column tile."""
+    probs = [W.random_box(n, 300 + i, box=(8.0, 8.0, 4.0), m=m, T=6.0) for i in range(B)]
+    pt = planner(probs[0], max_batch=B, precision="tf32x3")
+    pf = planner(probs[0], max_batch=B, precision="fp32")
+    xt, rt, kt = gpu_solve(pt, probs, 10)
+    xf, rf, kf = gpu_solve(pf, probs, 10)
+    assert rel_inf(xt, xf) < 5e-5, rel_inf(xt, xf)
+    M = oracle_mats(probs[0])
+    for i in [0, B - 1]:
+        st = oracle_solve(M, probs[i], 10)
+        assert rel_inf(xt[i].reshape(3, -1), st.xi) < XI_TOL
+
+
+def test_plain_tf32_runs_and_keeps_residual_scale():
+    probs = W.config4(4)
+    pt = planner(probs[0], "R3", max_batch=4, precision="tf32")
+    pf = planner(probs[0], "R3", max_batch=4, precision="fp32")
+    xt, rt, kt = gpu_solve(pt, probs, 20)
+    xf, rf, kf = gpu_solve(pf, probs, 20)
+    assert np.all(np.isfinite(xt)) and np.all(kt == 20)
+    assert np.all(rt < 2.0 * rf + 1e-3)
