@@ -135,6 +135,7 @@ amto_status launch_pair(amto_plan_s* pl, int batch, int init_mode, const float* 
                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 amto_status launch_rhs(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_apply(amto_plan_s* pl, int batch, cudaStream_t s);
+amto_status launch_splitk_reduce(amto_plan_s* pl, int batch, int splits, cudaStream_t s);
 // apply_tc.cu (tensor-core apply)
 size_t tc_smem_bytes();
 amto_status tc_configure(amto_plan_s* pl);

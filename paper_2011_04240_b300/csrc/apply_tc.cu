@@ -15,8 +15,8 @@
 //                   ("x3") correction that recovers float32 accuracy), or one
 //                   (plain TF32);
 //   all 4 warps     epilogue: tcgen05.ld of the accumulator, then either an
-//                   add into xi or a split-K partial, reduced in fixed order
-//                   by the last block of the tile.
+//                   add into xi or a split-K partial (summed in split order
+//                   by the separate reduce kernel).
 // All mbarrier waits are bounded; on timeout the block records an error in
 // the solve's control block, drains what it issued (bounded) and frees its
 // tensor memory.
@@ -105,7 +105,6 @@ struct TcArgs {
     float* xi;          // [N][M]
     const int* flags;
     float* ws;          // [splits][N][M]
-    unsigned* tickets;  // per output tile
     Ctl* ctl;
 };
 
@@ -116,7 +115,6 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long bars[2 * kTcStages + 1];
     __shared__ unsigned tmem_slot;
-    __shared__ int s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, kz = blockIdx.z;
     const int kbeg = kz * A.kper, kend = min(A.K, kbeg + A.kper);
@@ -237,23 +235,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN)
                      : "memory");
-    if (A.splits == 1 || !have) return;
-    // split-K: the last block of the tile adds the partials in split order
-    __threadfence();
-    __syncthreads();
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    if (tid == 0) s_last = (atomicAdd(A.tickets + tile, 1u) == (unsigned)(A.splits - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int e = tid; e < kBM * kBN; e += 128) {
-        const int col = n0 + e / kBM, r = m0 + e % kBM;
-        if (col >= N || r >= M || !(A.flags[col / 3] & FLAG_APPLY)) continue;
-        float sum = 0.f;
-        for (int z = 0; z < A.splits; ++z) sum += __ldcg(A.ws + ((size_t)z * N + col) * M + r);
-        A.xi[(size_t)col * M + r] += sum;
-    }
-    if (tid == 0) A.tickets[tile] = 0u;
+    // split-K partials are summed in split order by k_splitk_reduce
 }
 
 namespace {
@@ -320,7 +302,6 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     a.xi = pl->xi;
     a.flags = pl->flags;
     a.ws = pl->gemm_ws;
-    a.tickets = pl->gemm_tk;
     a.ctl = pl->ctl;
     const int tm = (a.M + kBM - 1) / kBM, tn = (a.N + kBN - 1) / kBN;
     int sp = pl->num_sms / (tm * tn);  // one wave of one-block-per-SM tiles
@@ -333,6 +314,7 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     k_apply_tc<<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(pl->tm_a_hi, pl->tm_a_lo,
                                                               pl->tm_b_hi, pl->tm_b_lo, a);
     AMTO_CUDA_TRY(cudaGetLastError());
+    if (sp > 1) return launch_splitk_reduce(pl, batch, sp, s);
     return AMTO_OK;
 }
 
