@@ -47,7 +47,65 @@ def parse():
                     help="run the timed solve from the host loop (no graph), as profilers need")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain per-instance line, cpu baseline and e2e leg")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving sweep only: Poisson arrivals of mixed agent counts against "
+                         "the continuous-batching server and the plain per-instance solve")
+    ap.add_argument("--rates", default="100,500,1000,2000,5000",
+                    help="arrival rates (req/s) of the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="arrival window of each serving run")
     return ap.parse_args()
+
+
+SERVE_SIZES = (8, 16, 32, 48, 64)
+SERVE_TOL, SERVE_MAX_ITERS = 1e-2, 1000
+
+
+def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
+    """One serving run at `rate` req/s: Poisson arrivals over `seconds` of
+    single problems with agent counts uniform in {8,16,32,48,64} (degree 10,
+    m = 100, random 8x8x4 m box), each solved to max residual < 1e-2 (or the
+    iteration cap).  Arm 1: the continuous-batching server (slots resident,
+    same-count batches through one cached-inverse GEMM, `precision` apply).
+    Arm 2: plain FP32 per-instance solves, one at a time in arrival order, on
+    the first `seq_cap` arrivals of the same list."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Planner, Server, amto
+    from paper_2011_04240_b300 import serving as SV
+    prec = {"fp32": amto.PREC_FP32, "tf32x3": amto.PREC_TF32X3, "tf32": amto.PREC_TF32}[precision]
+    arr = [(t, p.start, p.goal) for t, p in W.config5_arrivals(rate, seconds, seed)]
+    warm = [W.random_box(n, 99991 + n, box=(8.0, 8.0, 4.0)) for n in SERVE_SIZES]
+    sv = Server(SERVE_SIZES, m_steps=100, T=8.0, proj_mode=amto.PROJ_LITERAL, precision=prec,
+                max_slots=256, chunk_iters=8, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL)
+    try:
+        for p in warm:
+            t = sv.submit(p.start, p.goal)
+            while sv.poll(t, 1000) is None:
+                pass
+        slots = sv.stats()["slots"]
+        recs, wall = SV.run_arrivals(sv, arr)
+    finally:
+        sv.close()
+    out = {"rate_req_s": rate, "window_s": seconds,
+           "server": dict(SV.summarize(recs, wall), apply_precision=precision,
+                          slots={str(k): v for k, v in slots.items()})}
+    planners = {n: Planner(n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, max_batch=1)
+                for n in SERVE_SIZES}
+    try:
+        for p in warm:
+            planners[p.n].solve(torch.from_numpy(p.start[None]).cuda(),
+                                torch.from_numpy(p.goal[None]).cuda(), SERVE_MAX_ITERS, SERVE_TOL)
+        torch.cuda.synchronize()
+        sub = arr[:seq_cap]
+        recs2, wall2 = SV.run_sequential(planners, sub, SERVE_MAX_ITERS, SERVE_TOL)
+    finally:
+        for pl in planners.values():
+            pl.close()
+    out["plain_fp32_per_instance"] = dict(SV.summarize(recs2, wall2),
+                                          note=f"first {len(sub)} of the same arrivals")
+    return out
 
 
 def workload(args, rank):
@@ -266,6 +324,18 @@ def main():
     import torch
     import torch.distributed as dist
 
+    if args.serve:
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        runs = [serving_compare(float(r), args.serve_seconds, args.precision)
+                for r in args.rates.split(",")]
+        print(json.dumps({"metric": "serving: p50/p99 latency and instance-iterations/s",
+                          "workload": "Poisson arrivals, agent counts uniform in "
+                                      "{8,16,32,48,64}, degree 10, m=100, 8x8x4 m box, "
+                                      "tol 1e-2", "runs": runs}), flush=True)
+        return
+
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -363,6 +433,7 @@ def main():
                                                           "apply": kms[2] / max(kcnt[2], 1)}}
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
+            extras["serving"] = serving_compare(1000.0, 1.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -378,8 +449,9 @@ def main():
                                  f"{2 * pl.info.lambda_floats * 4 * B / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk.summary(),
-                # setup, initial projection, K x (rhs, apply, pair), FP64 residual, outputs
-                "gpu_launches": 3 * K + 4}
+                # setup, initial projection, K x (rhs, apply [+ split-K reduce], pair),
+                # FP64 residual, outputs
+                "gpu_launches": pl.info.launches_per_iteration * K + pl.info.launches_fixed}
         line.update(extras)
         print(json.dumps(line), flush=True)
     pl.close()

@@ -47,7 +47,8 @@ typedef enum {
     AMTO_ECUDA = 3,       /* a CUDA runtime call failed */
     AMTO_ENONFINITE = 4,  /* non-finite input or state */
     AMTO_ETIMEOUT = 5,    /* a bounded device wait ran out */
-    AMTO_ENUMERIC = 6     /* the KKT inverse failed its self-check */
+    AMTO_ENUMERIC = 6,    /* the KKT inverse failed its self-check */
+    AMTO_EPENDING = 7     /* a served request has not finished yet */
 } amto_status;
 
 /* Where lambda enters the alpha/beta/d steps (reading of Eqs. sphere_project
@@ -97,6 +98,11 @@ typedef struct {
     long long lambda_floats;            /* float32 multiplier slots per instance (one buffer) */
     double kkt_check;                   /* max |K K^-1 - I| of the FP64 inverse */
     size_t device_bytes;                /* device memory owned by the plan */
+    int launches_per_iteration;         /* kernels per iteration at batch = max_batch:
+                                           right-hand side, apply (+ split-K reduce),
+                                           pair step */
+    int launches_fixed;                 /* kernels per solve outside the loop: setup,
+                                           initial projection, FP64 residual, outputs */
 } amto_info;
 
 /*
@@ -224,6 +230,79 @@ amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count);
  * Results are identical in both modes.
  */
 amto_status amto_set_trace(amto_plan plan, int on);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of requests of mixed agent counts.
+ *
+ * The paper solves one problem at a time; this serving layer is the library's
+ * own.  A server keeps one plan per served agent count (the cached inverse of
+ * Remarks 1-2 is shared by all requests of that count) with a number of
+ * resident instance slots fixed by a device-memory budget.  A worker thread
+ * admits queued requests into free slots between iteration chunks while the
+ * other slots keep iterating, runs each agent count's resident slots as one
+ * batched step (one GEMM with the cached inverse per count and iteration; the
+ * counts on separate streams, overlapping on the device), and retires
+ * instances whose stopping rule fired.  A request's result does not depend
+ * on the other requests in flight.
+ * ------------------------------------------------------------------------ */
+typedef struct amto_server_s* amto_server;
+
+typedef struct {
+    int n_sizes;           /* number of served agent counts, 1..32 */
+    const int* sizes;      /* host [n_sizes] distinct agent counts */
+    int m_steps, poly_degree;
+    double T, a, b, rho;   /* as in amto_params; all six boundary conditions */
+    int proj_mode, precision;
+    int max_slots;         /* upper bound on resident instances per agent count */
+    int chunk_iters;       /* iterations between admission / retirement points */
+    int max_iters;         /* per-request iteration cap */
+    float tol;             /* per-request stopping tolerance on max ||f_c|| */
+    size_t memory_budget;  /* device bytes for resident per-instance state (xi, multipliers,
+                              partial sums, right-hand sides); 0 = half the free memory.
+                              Each agent count gets an equal share; its slot count is
+                              the number of instances whose state fits in it (at most
+                              max_slots).  Each count's cached inverse and the plan's
+                              fixed buffers come on top of the budget. */
+} amto_server_params;
+
+typedef struct {
+    int n_agents;          /* must be one of the served counts */
+    const float* start;    /* host [n][3]; copied by amto_server_submit */
+    const float* goal;     /* host [n][3] */
+} amto_request;
+
+typedef struct {
+    int iters;             /* iterations performed (-1: non-finite input or state;
+                              -2: a bounded wait in the iteration kernel gave up) */
+    float resid;           /* final max ||f_c||, recomputed in FP64 */
+    double t_submit, t_admit, t_done;  /* seconds on a monotonic clock */
+} amto_result_info;
+
+typedef struct {
+    long long completed, iterations, chunks;
+    int n_groups;
+    int sizes[32], slots[32];
+} amto_server_stats_t;
+
+/* Create a server and start its worker thread on the current device.
+ * Errors: EINVAL, ENOMEM (budget too small for one instance), ECUDA. */
+amto_status amto_server_create(const amto_server_params* params, amto_server* out);
+
+/* Queue one request (inputs are copied; non-blocking).  *ticket identifies it. */
+amto_status amto_server_submit(amto_server server, const amto_request* req, uint64_t* ticket);
+
+/* Collect a finished request: waits up to wait_ms for it, then returns
+ * AMTO_EPENDING if it is still running, or its status (AMTO_OK, ENONFINITE, ETIMEOUT)
+ * after copying xi (host [3][n][N+1], may be NULL) and *info (may be NULL).
+ * A collected ticket is forgotten. */
+amto_status amto_server_poll(amto_server server, uint64_t ticket, int wait_ms, float* xi_out,
+                             amto_result_info* info);
+
+/* Counters of the server (completed requests and their iterations, chunks). */
+amto_status amto_server_stats(amto_server server, amto_server_stats_t* out);
+
+/* Stop the worker (requests still queued are dropped) and free everything. */
+void amto_server_destroy(amto_server server);
 
 /* Thread-local text of the last error on this thread ("" if none). */
 const char* amto_last_error(void);

@@ -17,13 +17,13 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libamto.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
 STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",
-                4: "AMTO_ENONFINITE", 5: "AMTO_ETIMEOUT", 6: "AMTO_ENUMERIC"}
+                4: "AMTO_ENONFINITE", 5: "AMTO_ETIMEOUT", 6: "AMTO_ENUMERIC", 7: "AMTO_EPENDING"}
 
 
 class AmtoError(RuntimeError):
@@ -45,7 +45,35 @@ class Info(ctypes.Structure):
                 ("nb", ctypes.c_int), ("kkt_dim", ctypes.c_int), ("group", ctypes.c_int),
                 ("t_chunk", ctypes.c_int), ("n_chunks", ctypes.c_int),
                 ("lambda_floats", ctypes.c_longlong), ("kkt_check", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
+                ("launches_fixed", ctypes.c_int)]
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("n_sizes", ctypes.c_int), ("sizes", ctypes.POINTER(ctypes.c_int)),
+                ("m_steps", ctypes.c_int), ("poly_degree", ctypes.c_int),
+                ("T", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("rho", ctypes.c_double), ("proj_mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_slots", ctypes.c_int),
+                ("chunk_iters", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("tol", ctypes.c_float), ("memory_budget", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int), ("start", ctypes.c_void_p),
+                ("goal", ctypes.c_void_p)]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("resid", ctypes.c_float),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
+                ("chunks", ctypes.c_longlong), ("n_groups", ctypes.c_int),
+                ("sizes", ctypes.c_int * 32), ("slots", ctypes.c_int * 32)]
 
 
 _P = ctypes.c_void_p
@@ -62,6 +90,13 @@ SIGNATURES = {
     "amto_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int)]),
     "amto_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
+    "amto_server_create": (ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_P)]),
+    "amto_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "amto_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P,
+                                        ctypes.POINTER(ResultInfo)]),
+    "amto_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "amto_server_destroy": (None, [_P]),
     "amto_last_error": (ctypes.c_char_p, []),
     "amto_version": (ctypes.c_char_p, []),
 }
@@ -259,3 +294,76 @@ class Planner:
 
     def stats(self):
         return get_stats(self.plan)
+
+
+# ----------------------------------------------------------------------------
+# Serving (continuous batching; host inputs and outputs)
+# ----------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching server for requests of mixed agent counts.
+
+    Inputs are host numpy arrays; the server copies them at submit time.
+    poll() returns None while a request is running, else a dict with the
+    trajectories (numpy [3, n, N+1]), iterations, FP64 residual and the
+    submit / admission / completion times (seconds, monotonic clock).
+    """
+
+    def __init__(self, sizes, m_steps=100, T=8.0, a=0.6, b=1.2, rho=1.0, poly_degree=10,
+                 proj_mode=PROJ_LITERAL, precision=PREC_FP32, max_slots=64, chunk_iters=8,
+                 max_iters=2000, tol=1e-2, memory_budget=0):
+        import numpy as np
+        self._np = np
+        self.sizes = [int(x) for x in sizes]
+        self.nv = poly_degree + 1
+        arr = (ctypes.c_int * len(self.sizes))(*self.sizes)
+        self._sizes_arr = arr
+        prm = ServerParams(len(self.sizes), arr, m_steps, poly_degree, T, a, b, rho, proj_mode,
+                           precision, max_slots, chunk_iters, max_iters, tol, memory_budget)
+        h = _P()
+        _check(load().amto_server_create(ctypes.byref(prm), ctypes.byref(h)))
+        self.handle = h.value
+        self._n_of = {}
+
+    def submit(self, start, goal) -> int:
+        np = self._np
+        s = np.ascontiguousarray(start, dtype=np.float32)
+        g = np.ascontiguousarray(goal, dtype=np.float32)
+        n = s.shape[0]
+        req = Request(n, s.ctypes.data, g.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(load().amto_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._n_of[t.value] = n
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        np = self._np
+        n = self._n_of[ticket]
+        xi = np.empty((3, n, self.nv), dtype=np.float32)
+        info = ResultInfo()
+        st = load().amto_server_poll(self.handle, ticket, int(wait_ms), xi.ctypes.data,
+                                     ctypes.byref(info))
+        if st == EPENDING:
+            return None
+        del self._n_of[ticket]
+        if st not in (OK, ENONFINITE, ETIMEOUT):
+            raise AmtoError(st, last_error())
+        return {"status": st, "xi": xi, "iters": info.iters, "resid": info.resid,
+                "t_submit": info.t_submit, "t_admit": info.t_admit, "t_done": info.t_done}
+
+    def stats(self):
+        s = ServerStats()
+        _check(load().amto_server_stats(self.handle, ctypes.byref(s)))
+        return {"completed": s.completed, "iterations": s.iterations, "chunks": s.chunks,
+                "slots": {s.sizes[i]: s.slots[i] for i in range(s.n_groups)}}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().amto_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

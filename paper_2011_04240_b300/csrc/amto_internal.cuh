@@ -122,26 +122,35 @@ struct amto_plan_s {
 
 namespace amto {
 // precompute.cu
+// Checks of amto_params (no CUDA call); sets the error text on failure.
+amto_status validate_params(const amto_params& p);
 amto_status precompute(amto_plan_s* pl);
 // iterate.cu
 amto_status configure_kernels(amto_plan_s* pl);
 void gemm_workspace(const amto_plan_s* pl, size_t* ws_floats, int* tiles);
+// `list` (device, nlist entries) restricts a launch to those instances of the
+// plan's batch (continuous admission and retirement in the server).
 amto_status launch_setup(amto_plan_s* pl, int batch, const float* start, const float* goal,
                          const float* bc_extra, const float* xi_init, int max_iters, float tol,
-                         cudaStream_t s);
+                         cudaStream_t s, const int* list = nullptr, int nlist = 0);
 // init_mode 0: regular step; 1: initial projection, lambda = 0; 2: initial
 // projection with lambda gathered from `lambda_init`.
 amto_status launch_pair(amto_plan_s* pl, int batch, int init_mode, const float* lambda_init,
-                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s,
+                        const int* list = nullptr, int nlist = 0);
 amto_status launch_rhs(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_apply(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_splitk_reduce(amto_plan_s* pl, int batch, int splits, cudaStream_t s);
 // apply_tc.cu (tensor-core apply)
 size_t tc_smem_bytes();
 amto_status tc_configure(amto_plan_s* pl);
+// Tile grid, split-K count and K per split of the tensor-core apply.
+void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, int* kper);
+// Kernel launches of one iteration of a batch-`batch` solve.
+int launches_per_iteration(const amto_plan_s* pl, int batch);
 amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_final(amto_plan_s* pl, int batch, float* xi_out, float* resid_out,
-                         int* iters_out, cudaStream_t s);
+                         int* iters_out, cudaStream_t s, const int* list = nullptr, int nlist = 0);
 amto_status launch_state(amto_plan_s* pl, int batch, float* lambda_out, float* alpha_out,
                          float* beta_out, float* d_out, cudaStream_t s);
 }  // namespace amto

@@ -154,22 +154,9 @@ amto_status run_traced(amto_plan_s* pl, int batch, int max_iters, cudaStream_t s
 }
 
 }  // namespace
-}  // namespace amto
 
-using namespace amto;
-
-extern "C" {
-
-const char* amto_last_error(void) { return g_last_error.c_str(); }
-
-const char* amto_version(void) { return "amto 0.1 (sm_103a)"; }
-
-amto_status amto_create(const amto_params* prm, amto_plan* out) {
-    clear_error();
-    if (!out) return einval("out is NULL");
-    *out = nullptr;
-    if (!prm) return einval("params is NULL");
-    const amto_params& p = *prm;
+// Checks of amto_params shared by amto_create and the server (no CUDA call).
+amto_status validate_params(const amto_params& p) {
     if (p.n_agents < 2 || p.n_agents > 256) return einval("n_agents must be in [2, 256]");
     if (p.poly_degree < 2 || p.poly_degree > 15) return einval("poly_degree must be in [2, 15]");
     if (p.m_steps < p.poly_degree + 1 || p.m_steps > 4096)
@@ -188,6 +175,26 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
         p.precision != AMTO_PREC_TF32)
         return einval("precision: AMTO_PREC_FP32, AMTO_PREC_TF32X3 and AMTO_PREC_TF32 are available");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
+    return AMTO_OK;
+}
+
+}  // namespace amto
+
+using namespace amto;
+
+extern "C" {
+
+const char* amto_last_error(void) { return g_last_error.c_str(); }
+
+const char* amto_version(void) { return "amto 0.1 (sm_103a)"; }
+
+amto_status amto_create(const amto_params* prm, amto_plan* out) {
+    clear_error();
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (!prm) return einval("params is NULL");
+    const amto_params& p = *prm;
+    if (amto::validate_params(p) != AMTO_OK) return AMTO_EINVAL;
 
     amto_plan_s* pl = new (std::nothrow) amto_plan_s();
     if (!pl) {
@@ -205,6 +212,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->m = p.m_steps;
     pl->N = p.poly_degree;
     pl->nv = p.poly_degree + 1;
+    const int nb = __builtin_popcount(p.bc_mask);
     pl->nb = nb;
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
@@ -357,6 +365,8 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->lambda_floats = plan->geo.lam_floats;
     out->kkt_check = plan->kkt_check;
     out->device_bytes = plan->bytes;
+    out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
+    out->launches_fixed = 4;
     return AMTO_OK;
 }
 

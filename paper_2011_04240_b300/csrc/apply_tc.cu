@@ -293,6 +293,21 @@ amto_status tc_configure(amto_plan_s* pl) {
     return st;
 }
 
+void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, int* kper) {
+    const int M = pl->n * pl->nv, N = 3 * batch, K = pl->kdim;
+    *tm = (M + kBM - 1) / kBM;
+    *tn = (N + kBN - 1) / kBN;
+    // the split over K is fixed by the plan's largest batch, so a column's
+    // summation order (hence its result) does not depend on the batch size
+    const int tn_max = (3 * pl->prm.max_batch + kBN - 1) / kBN;
+    int sp = pl->num_sms / (*tm * tn_max);  // one wave of one-block-per-SM tiles
+    sp = sp < 1 ? 1 : (sp > 8 ? 8 : sp);
+    int kp = (K + sp - 1) / sp;
+    kp = (kp + kBK - 1) / kBK * kBK;
+    *splits = (K + kp - 1) / kp;
+    *kper = kp;
+}
+
 amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     TcArgs a{};
     a.M = pl->n * pl->nv;
@@ -303,13 +318,8 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     a.flags = pl->flags;
     a.ws = pl->gemm_ws;
     a.ctl = pl->ctl;
-    const int tm = (a.M + kBM - 1) / kBM, tn = (a.N + kBN - 1) / kBN;
-    int sp = pl->num_sms / (tm * tn);  // one wave of one-block-per-SM tiles
-    sp = sp < 1 ? 1 : (sp > 8 ? 8 : sp);
-    int kp = (a.K + sp - 1) / sp;
-    kp = (kp + kBK - 1) / kBK * kBK;
-    sp = (a.K + kp - 1) / kp;
-    a.kper = kp;
+    int tm, tn, sp;
+    tc_shape(pl, batch, &tm, &tn, &sp, &a.kper);
     a.splits = sp;
     k_apply_tc<<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(pl->tm_a_hi, pl->tm_a_lo,
                                                               pl->tm_b_hi, pl->tm_b_lo, a);

@@ -1,0 +1,548 @@
+// Serving form: continuous batching of planning requests of mixed agent counts.
+//
+// A server keeps one plan (cached KKT inverse, Remarks 1-2) per served agent
+// count and a fixed number of resident instance slots per plan, sized from a
+// device-memory budget.  A worker thread drives the GPU:
+//   - newly submitted requests wait in a per-count queue and are admitted
+//     into free slots between iteration chunks (the other slots keep their
+//     state and keep iterating): a subset setup (boundary values, initial
+//     trajectories) and a subset initial projection run for the admitted
+//     slots only;
+//   - every chunk, each agent-count group runs C iterations of Algorithm 1
+//     for all of its resident slots as one batched step (one K^-1 GEMM per
+//     group and iteration), each group on its own CUDA stream so the groups'
+//     work overlaps on the device;
+//   - after the chunk, slots whose stopping rule fired are retired: their
+//     FP64 residual and trajectories are copied to host memory and the slot
+//     is freed for the next request.
+// Each instance's arithmetic depends only on its own inputs and the shared
+// plan (the batched apply computes every column independently, and all
+// reductions have a fixed order), so a request's result is the same alone
+// and in any mix.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "amto_internal.cuh"
+
+namespace amto {
+
+// Device bytes of one resident instance of a plan (the state amto_create
+// allocates per unit of max_batch).
+size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision) {
+    const PairGeom g = choose_geometry(n, m);
+    const int nv = degree + 1, nb = __builtin_popcount(bc_mask);
+    const size_t kdim = (size_t)n * (nv + nb), kp = (kdim + 3) / 4 * 4, nvn = (size_t)n * nv;
+    size_t b = 0;
+    b += 4 * 3 * nvn;                          // xi
+    b += 4 * 3 * (size_t)n * nb;               // b_eq
+    b += 2 * 4 * (size_t)g.lam_floats;         // multipliers (two buffers)
+    b += 4 * (size_t)g.n_chunks * 3 * nvn;     // unit partials
+    b += 4 * (size_t)g.n_chunks;
+    b += 4 * 3 * kp * (precision == AMTO_PREC_FP32 ? 1 : 2);  // right-hand side(s)
+    b += 4 * 8 * 3 * nvn;                      // split-K workspace share
+    b += 32;                                   // flags, counters
+    return b;
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+    return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Pending {
+    uint64_t ticket;
+    std::vector<float> start, goal;
+    double t_submit;
+};
+
+struct Result {
+    int status = AMTO_EPENDING;
+    int iters = 0;
+    float resid = 0.f;
+    std::vector<float> xi;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+struct Group {
+    int n = 0, S = 0, nv = 0;
+    amto_plan plan = nullptr;
+    cudaStream_t stream = nullptr;
+    float *d_start = nullptr, *d_goal = nullptr, *d_xi = nullptr, *d_resid = nullptr;
+    int *d_iters = nullptr, *d_list = nullptr;
+    float *h_start = nullptr, *h_goal = nullptr, *h_xi = nullptr, *h_resid = nullptr;
+    int *h_iters = nullptr, *h_flags = nullptr, *h_list = nullptr;
+    // chunk graphs over slot prefixes [0, pre[k]) (pre ascending, last = S):
+    // admission fills the lowest free slots, so at low load a chunk launches
+    // over a short prefix instead of all S slots
+    std::vector<int> pre;
+    std::vector<cudaGraphExec_t> chunk;
+    int launched = 0;                   // prefix of the chunk in flight
+    cudaEvent_t done_ev = nullptr;
+    std::vector<int64_t> slot_ticket;   // -1: free
+    std::vector<double> slot_admit;
+    std::deque<Pending> queue;
+    int active = 0;
+};
+
+}  // namespace
+}  // namespace amto
+
+struct amto_server_s {
+    amto_server_params prm;
+    std::vector<int> sizes;
+    std::vector<std::unique_ptr<amto::Group>> groups;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::unordered_map<int, int> group_of_n;
+    std::vector<std::deque<amto::Pending>> inbox;  // per group, guarded by mu
+    std::unordered_map<uint64_t, amto::Result> results;  // guarded by mu
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    int device = 0;
+    // statistics (guarded by mu)
+    long long done_count = 0, done_iters = 0, chunks = 0;
+    int worker_error = AMTO_OK;
+    std::string worker_msg;
+};
+
+namespace amto {
+namespace {
+
+amto_params plan_params(const amto_server_params& p, int n, int slots) {
+    amto_params ap{};
+    ap.n_agents = n;
+    ap.m_steps = p.m_steps;
+    ap.poly_degree = p.poly_degree;
+    ap.T = p.T;
+    ap.a = p.a;
+    ap.b = p.b;
+    ap.rho = p.rho;
+    ap.bc_mask = AMTO_BC_ALL;
+    ap.proj_mode = p.proj_mode;
+    ap.precision = p.precision;
+    ap.max_batch = slots;
+    return ap;
+}
+
+amto_status group_init(amto_server_s* sv, Group& g, int n, int slots) {
+    const amto_server_params& p = sv->prm;
+    g.n = n;
+    g.S = slots;
+    g.nv = p.poly_degree + 1;
+    const amto_params ap = plan_params(p, n, slots);
+    amto_status st = amto_create(&ap, &g.plan);
+    if (st != AMTO_OK) return st;
+    amto_plan_s* pl = g.plan;
+    const size_t in = (size_t)slots * n * 3, out = (size_t)slots * 3 * n * g.nv;
+    AMTO_CUDA_TRY(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    AMTO_CUDA_TRY(cudaEventCreateWithFlags(&g.done_ev, cudaEventDisableTiming));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_start, 4 * in));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_goal, 4 * in));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_xi, 4 * out));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_resid, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_iters, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_list, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_start, 4 * in));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_goal, 4 * in));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_xi, 4 * out));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_resid, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_iters, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_flags, 4 * (size_t)slots));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_list, 4 * (size_t)slots));
+    g.slot_ticket.assign(slots, -1);
+    g.slot_admit.assign(slots, 0.0);
+    // every slot starts free (flagged done, skipped by all kernels); the
+    // group's stopping rule lives in the plan's control block
+    std::vector<int> fl(slots, FLAG_DONE);
+    AMTO_CUDA_TRY(cudaMemcpy(pl->flags, fl.data(), 4 * (size_t)slots, cudaMemcpyHostToDevice));
+    Ctl c{};
+    c.max_iters = p.max_iters;
+    c.tol = p.tol;
+    c.batch = slots;
+    AMTO_CUDA_TRY(cudaMemcpy(pl->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    // chunk graphs: C iterations of the batched step over slot prefixes 8,
+    // 16, 32, ... and S (the apply's split over K is fixed by S, so a slot's
+    // arithmetic is the same in every prefix)
+    for (int q = 8; q < slots; q *= 2) g.pre.push_back(q);
+    g.pre.push_back(slots);
+    for (int q : g.pre) {
+        cudaGraph_t graph;
+        AMTO_CUDA_TRY(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < p.chunk_iters && st == AMTO_OK; ++it) {
+            st = launch_rhs(pl, q, g.stream);
+            if (st == AMTO_OK) st = launch_apply(pl, q, g.stream);
+            if (st == AMTO_OK) st = launch_pair(pl, q, 0, nullptr, 0, 0, g.stream);
+        }
+        cudaError_t ce = cudaStreamEndCapture(g.stream, &graph);
+        if (st != AMTO_OK) return st;
+        if (ce != cudaSuccess) {
+            set_error("server: capture of the iteration chunk failed");
+            return AMTO_ECUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        ce = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            set_error("server: instantiating the iteration chunk failed");
+            return AMTO_ECUDA;
+        }
+        g.chunk.push_back(ex);
+    }
+    return AMTO_OK;
+}
+
+void group_free(Group& g) {
+    for (cudaGraphExec_t ex : g.chunk) cudaGraphExecDestroy(ex);
+    if (g.done_ev) cudaEventDestroy(g.done_ev);
+    void* d[] = {g.d_start, g.d_goal, g.d_xi, g.d_resid, g.d_iters, g.d_list};
+    for (void* p : d)
+        if (p) cudaFree(p);
+    void* h[] = {g.h_start, g.h_goal, g.h_xi, g.h_resid, g.h_iters, g.h_flags, g.h_list};
+    for (void* p : h)
+        if (p) cudaFreeHost(p);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.plan) amto_destroy(g.plan);
+}
+
+// Admit queued requests into free slots of one group (worker thread).
+amto_status admit(amto_server_s* sv, Group& g) {
+    int cnt = 0;
+    const int n = g.n;
+    for (int s = 0; s < g.S && !g.queue.empty(); ++s) {
+        if (g.slot_ticket[s] >= 0) continue;
+        Pending p = std::move(g.queue.front());
+        g.queue.pop_front();
+        memcpy(g.h_start + (size_t)s * n * 3, p.start.data(), 4 * (size_t)n * 3);
+        memcpy(g.h_goal + (size_t)s * n * 3, p.goal.data(), 4 * (size_t)n * 3);
+        g.slot_ticket[s] = (int64_t)p.ticket;
+        g.slot_admit[s] = now_s();
+        g.h_list[cnt++] = s;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->results[p.ticket].t_admit = g.slot_admit[s];
+        }
+    }
+    if (cnt == 0) return AMTO_OK;
+    g.active += cnt;
+    const size_t row = 4 * (size_t)n * 3;
+    for (int i = 0; i < cnt; ++i) {
+        const int s = g.h_list[i];
+        AMTO_CUDA_TRY(cudaMemcpyAsync(g.d_start + (size_t)s * n * 3, g.h_start + (size_t)s * n * 3,
+                                      row, cudaMemcpyHostToDevice, g.stream));
+        AMTO_CUDA_TRY(cudaMemcpyAsync(g.d_goal + (size_t)s * n * 3, g.h_goal + (size_t)s * n * 3,
+                                      row, cudaMemcpyHostToDevice, g.stream));
+    }
+    AMTO_CUDA_TRY(cudaMemcpyAsync(g.d_list, g.h_list, 4 * (size_t)cnt, cudaMemcpyHostToDevice,
+                                  g.stream));
+    amto_plan_s* pl = g.plan;
+    amto_status st = launch_setup(pl, g.S, g.d_start, g.d_goal, nullptr, nullptr,
+                                  sv->prm.max_iters, sv->prm.tol, g.stream, g.d_list, cnt);
+    if (st == AMTO_OK) st = launch_pair(pl, g.S, 1, nullptr, 0, 0, g.stream, g.d_list, cnt);
+    return st;
+}
+
+// Retire finished slots of one group (worker thread, after its chunk).
+amto_status retire(amto_server_s* sv, Group& g) {
+    amto_plan_s* pl = g.plan;
+    int cnt = 0;
+    for (int s = 0; s < g.launched; ++s)
+        if (g.slot_ticket[s] >= 0 && (g.h_flags[s] & FLAG_DONE)) g.h_list[cnt++] = s;
+    if (cnt == 0) return AMTO_OK;
+    AMTO_CUDA_TRY(cudaMemcpyAsync(g.d_list, g.h_list, 4 * (size_t)cnt, cudaMemcpyHostToDevice,
+                                  g.stream));
+    amto_status st = launch_final(pl, g.S, g.d_xi, g.d_resid, g.d_iters, g.stream, g.d_list, cnt);
+    if (st != AMTO_OK) return st;
+    const size_t xrow = (size_t)3 * g.n * g.nv;
+    for (int i = 0; i < cnt; ++i) {
+        const int s = g.h_list[i];
+        AMTO_CUDA_TRY(cudaMemcpyAsync(g.h_xi + s * xrow, g.d_xi + s * xrow, 4 * xrow,
+                                      cudaMemcpyDeviceToHost, g.stream));
+    }
+    AMTO_CUDA_TRY(cudaMemcpyAsync(g.h_resid, g.d_resid, 4 * (size_t)g.launched,
+                                  cudaMemcpyDeviceToHost, g.stream));
+    AMTO_CUDA_TRY(cudaMemcpyAsync(g.h_iters, g.d_iters, 4 * (size_t)g.launched,
+                                  cudaMemcpyDeviceToHost, g.stream));
+    AMTO_CUDA_TRY(cudaStreamSynchronize(g.stream));
+    const double t = now_s();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int i = 0; i < cnt; ++i) {
+        const int s = g.h_list[i];
+        Result& r = sv->results[(uint64_t)g.slot_ticket[s]];
+        r.iters = g.h_iters[s];
+        r.resid = g.h_resid[s];
+        r.xi.assign(g.h_xi + s * xrow, g.h_xi + (s + 1) * xrow);
+        r.t_done = t;
+        r.status = r.iters == -2 ? AMTO_ETIMEOUT : r.iters < 0 ? AMTO_ENONFINITE : AMTO_OK;
+        sv->done_count += 1;
+        sv->done_iters += r.iters > 0 ? r.iters : 0;
+        g.slot_ticket[s] = -1;
+    }
+    g.active -= cnt;
+    sv->cv.notify_all();
+    return AMTO_OK;
+}
+
+void worker_main(amto_server_s* sv) {
+    cudaSetDevice(sv->device);
+    amto_status st = AMTO_OK;
+    while (st == AMTO_OK) {
+        bool any = false;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            auto has_work = [&] {
+                if (sv->stop) return true;
+                for (size_t i = 0; i < sv->groups.size(); ++i)
+                    if (!sv->inbox[i].empty() || sv->groups[i]->active > 0 ||
+                        !sv->groups[i]->queue.empty())
+                        return true;
+                return false;
+            };
+            sv->cv.wait_for(lk, std::chrono::milliseconds(50), has_work);
+            if (sv->stop) break;
+            for (size_t i = 0; i < sv->groups.size(); ++i) {
+                auto& q = sv->inbox[i];
+                while (!q.empty()) {
+                    sv->groups[i]->queue.push_back(std::move(q.front()));
+                    q.pop_front();
+                }
+            }
+        }
+        // admit, then one chunk per group with resident work (groups overlap)
+        for (auto& gp : sv->groups) {
+            Group& g = *gp;
+            if (st == AMTO_OK) st = admit(sv, g);
+            if (st == AMTO_OK && g.active > 0) {
+                any = true;
+                int hi = 0;
+                for (int s = 0; s < g.S; ++s)
+                    if (g.slot_ticket[s] >= 0) hi = s + 1;
+                size_t k = 0;
+                while (g.pre[k] < hi) ++k;
+                g.launched = g.pre[k];
+                if (cudaGraphLaunch(g.chunk[k], g.stream) != cudaSuccess) {
+                    set_error("server: chunk launch failed");
+                    st = AMTO_ECUDA;
+                }
+                cudaMemcpyAsync(g.h_flags, g.plan->flags, 4 * (size_t)g.launched,
+                                cudaMemcpyDeviceToHost, g.stream);
+                cudaEventRecord(g.done_ev, g.stream);
+            }
+        }
+        if (!any) continue;
+        for (auto& gp : sv->groups) {
+            Group& g = *gp;
+            if (st != AMTO_OK || g.active == 0) continue;
+            if (cudaEventSynchronize(g.done_ev) != cudaSuccess) {
+                set_error("server: device error during a chunk");
+                st = AMTO_ECUDA;
+                break;
+            }
+            st = retire(sv, g);
+        }
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->chunks += 1;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (st != AMTO_OK) {
+        sv->worker_error = st;
+        sv->worker_msg = amto_last_error();
+        for (auto& kv : sv->results)
+            if (kv.second.status == AMTO_EPENDING) kv.second.status = st;
+    }
+    sv->cv.notify_all();
+}
+
+}  // namespace
+}  // namespace amto
+
+using namespace amto;
+
+extern "C" {
+
+amto_status amto_server_create(const amto_server_params* prm, amto_server* out) {
+    clear_error();
+    if (!out || !prm) {
+        set_error("invalid argument: params and out are required");
+        return AMTO_EINVAL;
+    }
+    *out = nullptr;
+    const amto_server_params& p = *prm;
+    if (p.n_sizes < 1 || p.n_sizes > 32 || !p.sizes) {
+        set_error("invalid argument: 1..32 agent counts are required");
+        return AMTO_EINVAL;
+    }
+    if (p.chunk_iters < 1 || p.chunk_iters > 1024 || p.max_iters < 1 || !(p.tol >= 0.f)) {
+        set_error("invalid argument: chunk_iters in [1, 1024], max_iters >= 1, tol >= 0");
+        return AMTO_EINVAL;
+    }
+    if (p.max_slots < 1 || p.max_slots > 65535) {
+        set_error("invalid argument: max_slots must be in [1, 65535]");
+        return AMTO_EINVAL;
+    }
+    for (int i = 0; i < p.n_sizes; ++i) {
+        for (int j = 0; j < i; ++j)
+            if (p.sizes[i] == p.sizes[j]) {
+                set_error("invalid argument: agent counts must be distinct");
+                return AMTO_EINVAL;
+            }
+        if (validate_params(plan_params(p, p.sizes[i], p.max_slots)) != AMTO_OK)
+            return AMTO_EINVAL;
+    }
+    amto_server_s* sv = new (std::nothrow) amto_server_s();
+    if (!sv) {
+        set_error("host allocation failed");
+        return AMTO_ENOMEM;
+    }
+    sv->prm = p;
+    sv->sizes.assign(p.sizes, p.sizes + p.n_sizes);
+    cudaGetDevice(&sv->device);
+    // admission by device memory: each agent count gets an equal share of the
+    // budget; its slot count is the number of resident instances that fit
+    size_t budget = p.memory_budget;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = fr / 2;
+    }
+    const size_t share = budget / p.n_sizes;
+    amto_status st = AMTO_OK;
+    sv->inbox.resize(p.n_sizes);
+    for (int i = 0; i < p.n_sizes && st == AMTO_OK; ++i) {
+        const int n = p.sizes[i];
+        const size_t per = instance_bytes(n, p.m_steps, p.poly_degree, AMTO_BC_ALL, p.precision);
+        long long slots = (long long)(share / per);
+        if (slots > p.max_slots) slots = p.max_slots;
+        if (slots < 1) {
+            set_error("server: the memory budget does not fit one instance of " + std::to_string(n) +
+                      " agents");
+            st = AMTO_ENOMEM;
+            break;
+        }
+        sv->groups.emplace_back(new Group());
+        sv->group_of_n[n] = i;
+        st = group_init(sv, *sv->groups.back(), n, (int)slots);
+    }
+    if (st != AMTO_OK) {
+        std::string keep = amto_last_error();
+        for (auto& g : sv->groups) group_free(*g);
+        delete sv;
+        set_error(keep);
+        return st;
+    }
+    sv->worker = std::thread(worker_main, sv);
+    *out = sv;
+    return AMTO_OK;
+}
+
+amto_status amto_server_submit(amto_server sv, const amto_request* req, uint64_t* ticket) {
+    clear_error();
+    if (!sv || !req || !ticket || !req->start || !req->goal) {
+        set_error("invalid argument: server, request (with start and goal) and ticket are required");
+        return AMTO_EINVAL;
+    }
+    auto it = sv->group_of_n.find(req->n_agents);
+    if (it == sv->group_of_n.end()) {
+        set_error("invalid argument: this server does not serve " + std::to_string(req->n_agents) +
+                  " agents");
+        return AMTO_EINVAL;
+    }
+    Pending p;
+    p.start.assign(req->start, req->start + (size_t)req->n_agents * 3);
+    p.goal.assign(req->goal, req->goal + (size_t)req->n_agents * 3);
+    p.t_submit = now_s();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->worker_error != AMTO_OK) {
+        set_error("server worker stopped: " + sv->worker_msg);
+        return (amto_status)sv->worker_error;
+    }
+    p.ticket = sv->next_ticket++;
+    Result r;
+    r.t_submit = p.t_submit;
+    sv->results[p.ticket] = std::move(r);
+    *ticket = p.ticket;
+    sv->inbox[it->second].push_back(std::move(p));
+    sv->cv.notify_all();
+    return AMTO_OK;
+}
+
+amto_status amto_server_poll(amto_server sv, uint64_t ticket, int wait_ms, float* xi_out,
+                             amto_result_info* info) {
+    clear_error();
+    if (!sv) {
+        set_error("invalid argument: server is NULL");
+        return AMTO_EINVAL;
+    }
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) {
+        set_error("invalid argument: unknown or already collected ticket");
+        return AMTO_EINVAL;
+    }
+    if (it->second.status == AMTO_EPENDING && wait_ms > 0) {
+        // look the ticket up again after every wake-up: a submit in between
+        // may rehash the map and invalidate iterators
+        sv->cv.wait_for(lk, std::chrono::milliseconds(wait_ms),
+                        [&] { return sv->results.at(ticket).status != AMTO_EPENDING; });
+        it = sv->results.find(ticket);
+    }
+    Result& r = it->second;
+    if (r.status == AMTO_EPENDING) return AMTO_EPENDING;
+    if (info) {
+        info->iters = r.iters;
+        info->resid = r.resid;
+        info->t_submit = r.t_submit;
+        info->t_admit = r.t_admit;
+        info->t_done = r.t_done;
+    }
+    if (xi_out && !r.xi.empty()) memcpy(xi_out, r.xi.data(), 4 * r.xi.size());
+    const amto_status st = (amto_status)r.status;
+    sv->results.erase(it);
+    return st;
+}
+
+amto_status amto_server_stats(amto_server sv, amto_server_stats_t* out) {
+    clear_error();
+    if (!sv || !out) {
+        set_error("invalid argument: server and out are required");
+        return AMTO_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    out->completed = sv->done_count;
+    out->iterations = sv->done_iters;
+    out->chunks = sv->chunks;
+    out->n_groups = (int)sv->groups.size();
+    for (int i = 0; i < (int)sv->groups.size() && i < 32; ++i) {
+        out->sizes[i] = sv->groups[i]->n;
+        out->slots[i] = sv->groups[i]->S;
+    }
+    return AMTO_OK;
+}
+
+void amto_server_destroy(amto_server sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    cudaDeviceSynchronize();
+    for (auto& g : sv->groups) group_free(*g);
+    delete sv;
+}
+
+}  // extern "C"

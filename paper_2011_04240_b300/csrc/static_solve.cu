@@ -131,6 +131,7 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     // a view of the plan whose workspace pointers point into the scratch
     amto_plan_s v;
     v.prm = pl.prm;
+    v.prm.max_batch = 1;  // one instance: the apply runs as the matrix-vector kernel
     v.device = pl.device;
     v.num_sms = pl.num_sms;
     v.n = pl.n; v.m = pl.m; v.N = pl.N; v.nv = pl.nv; v.nb = pl.nb; v.kdim = pl.kdim; v.p = pl.p;

@@ -73,3 +73,39 @@ def test_null_arguments_rejected(lib):
     assert lib.amto_set_trace(None, 1) == amto.EINVAL
     lib.amto_destroy(None)  # no-op
     assert lib.amto_version().decode().startswith("amto")
+
+
+def _server_params(**kw):
+    from paper_2011_04240_b300 import amto
+    sizes = kw.pop("sizes", (8, 16))
+    arr = (ctypes.c_int * len(sizes))(*sizes)
+    base = dict(n_sizes=len(sizes), sizes=arr, m_steps=100, poly_degree=10, T=8.0, a=0.6,
+                b=1.2, rho=1.0, proj_mode=0, precision=0, max_slots=8, chunk_iters=4,
+                max_iters=100, tol=1e-2, memory_budget=0)
+    base.update(kw)
+    return amto.ServerParams(**base), arr
+
+
+@pytest.mark.parametrize("bad", [dict(sizes=()), dict(sizes=(8, 8)), dict(sizes=(1,)),
+                                 dict(sizes=(8, 300)), dict(chunk_iters=0), dict(max_iters=0),
+                                 dict(tol=float("nan")), dict(max_slots=0), dict(m_steps=5),
+                                 dict(precision=9), dict(proj_mode=3), dict(n_sizes=40)])
+def test_server_create_rejects_invalid_params(lib, bad):
+    """Checked before any device call, so this runs without a GPU."""
+    from paper_2011_04240_b300 import amto
+    prm, _keep = _server_params(**bad)
+    h = ctypes.c_void_p()
+    st = lib.amto_server_create(ctypes.byref(prm), ctypes.byref(h))
+    assert st == amto.EINVAL
+    assert h.value is None
+    assert "invalid argument" in lib.amto_last_error().decode()
+
+
+def test_server_null_arguments_rejected(lib):
+    from paper_2011_04240_b300 import amto
+    t = ctypes.c_uint64()
+    assert lib.amto_server_create(None, None) == amto.EINVAL
+    assert lib.amto_server_submit(None, None, ctypes.byref(t)) == amto.EINVAL
+    assert lib.amto_server_poll(None, 1, 0, None, None) == amto.EINVAL
+    assert lib.amto_server_stats(None, None) == amto.EINVAL
+    lib.amto_server_destroy(None)  # no-op

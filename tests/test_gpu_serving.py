@@ -1,0 +1,131 @@
+"""Serving form: continuous batching of mixed agent counts (amto_server_*).
+
+Requests are admitted into resident slots between iteration chunks while
+other requests keep iterating; each result must be the same alone and in a
+mix (every instance's arithmetic depends only on its own inputs and the
+shared plan), must match the FP64 oracle at a fixed iteration count, and
+must stop by the rule of Algorithm 1 (residual below tol, or max_iters).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_helpers import oracle_mats, oracle_solve, planner, gpu_solve, rel_inf
+
+pytestmark = pytest.mark.gpu
+PREC = {"fp32": 0, "tf32x3": 1}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _server(sizes, precision="fp32", **kw):
+    from paper_2011_04240_b300 import Server
+    base = dict(m_steps=100, T=8.0, proj_mode=0, precision=PREC[precision], max_slots=8,
+                chunk_iters=4, max_iters=300, tol=1e-2)
+    base.update(kw)
+    return Server(sizes, **base)
+
+
+def _collect(sv, tickets):
+    out = {}
+    for t in tickets:
+        r = None
+        while r is None:
+            r = sv.poll(t, 2000)
+        out[t] = r
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_same_result_alone_and_in_mix(precision):
+    sizes = (8, 16, 24)
+    sv = _server(sizes, precision)
+    try:
+        probe = W.random_box(16, 4242, box=(8.0, 8.0, 4.0))
+        alone = _collect(sv, [sv.submit(probe.start, probe.goal)])
+        (ra,) = alone.values()
+        mix = [W.random_box(int(sizes[i % 3]), 7000 + i, box=(8.0, 8.0, 4.0)) for i in range(30)]
+        tickets = [sv.submit(p.start, p.goal) for p in mix[:17]]
+        # the probe arrives while the first requests are resident and iterating
+        tp = sv.submit(probe.start, probe.goal)
+        tickets += [sv.submit(p.start, p.goal) for p in mix[17:]]
+        res = _collect(sv, tickets + [tp])
+        rm = res[tp]
+        assert rm["iters"] == ra["iters"]
+        assert rel_inf(rm["xi"], ra["xi"]) <= 1e-6
+        assert abs(rm["resid"] - ra["resid"]) <= 1e-6 * max(1.0, abs(ra["resid"]))
+        # every request finished by the stopping rule, and was admitted after submit
+        for t in tickets:
+            r = res[t]
+            assert r["status"] == 0
+            assert 1 <= r["iters"] <= 300
+            assert r["iters"] == 300 or r["resid"] < 1e-2 * 1.5
+            assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        st = sv.stats()
+        assert st["completed"] == 32
+        assert set(st["slots"]) == set(sizes)
+    finally:
+        sv.close()
+
+
+def test_fixed_iterations_match_oracle_and_batch_solve():
+    """tol = 0: every request runs exactly max_iters iterations; compare with
+    the FP64 oracle (xi parity tolerance) and the batched plain solve."""
+    sv = _server((5, 12), "fp32", max_iters=10, tol=0.0, chunk_iters=3)
+    try:
+        probs = [W.random_box(5 if i % 2 else 12, 900 + i, box=(8.0, 8.0, 4.0)) for i in range(8)]
+        tk = [sv.submit(p.start, p.goal) for p in probs]
+        res = _collect(sv, tk)
+        for t, p in zip(tk, probs):
+            r = res[t]
+            assert r["iters"] == 10
+            st = oracle_solve(oracle_mats(p), p, 10)
+            assert rel_inf(r["xi"].reshape(3, -1), st.xi) < 1e-4
+        p = probs[1]
+        xs, _, ks = gpu_solve(planner(p, max_batch=1), [p], 10)
+        assert ks[0] == 10
+        assert rel_inf(res[tk[1]]["xi"], xs[0]) < 1e-5
+    finally:
+        sv.close()
+
+
+def test_memory_budget_sets_slots_and_queues():
+    """A budget of about two instances per count: requests wait for free
+    slots and still all complete."""
+    from paper_2011_04240_b300 import Server, AmtoError
+    from paper_2011_04240_b300.amto import ENOMEM
+    with pytest.raises(AmtoError) as e:
+        Server((8,), max_iters=20, memory_budget=1024)
+    assert e.value.status == ENOMEM
+    # about 0.38 MB of resident state per 16-agent instance, 0.11 MB per
+    # 8-agent one: an 0.8 MB share holds two 16-agent slots
+    sv = _server((8, 16), max_iters=20, tol=0.0, max_slots=1000, memory_budget=1_600_000)
+    try:
+        st = sv.stats()
+        assert 1 <= st["slots"][16] <= 4 and 1 <= st["slots"][8] <= 16, st
+        probs = [W.random_box(8 if i % 2 else 16, 50 + i, box=(8.0, 8.0, 4.0)) for i in range(12)]
+        res = _collect(sv, [sv.submit(p.start, p.goal) for p in probs])
+        assert all(r["iters"] == 20 for r in res.values())
+        assert sv.stats()["completed"] == 12
+    finally:
+        sv.close()
+
+
+def test_rejects_unserved_size_and_unknown_ticket():
+    from paper_2011_04240_b300 import AmtoError
+    from paper_2011_04240_b300 import amto as A
+    sv = _server((8,), max_iters=5)
+    try:
+        p = W.random_box(16, 1, box=(8.0, 8.0, 4.0))
+        with pytest.raises(AmtoError):
+            sv.submit(p.start, p.goal)
+        st = A.load().amto_server_poll(sv.handle, 987654321, 0, None, None)
+        assert st == A.EINVAL
+    finally:
+        sv.close()

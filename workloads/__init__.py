@@ -69,16 +69,18 @@ def _reject_points(rng: np.random.Generator, n: int, lo, hi, min_sep: float,
     """n points uniform in the box [lo, hi] with pairwise distance >= min_sep."""
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
-    pts = []
+    pts = np.empty((n, 3))
+    k = 0
     tries = 0
-    while len(pts) < n:
+    while k < n:
         tries += 1
         if tries > max_tries:
             raise RuntimeError("rejection sampler could not place all agents")
         c = lo + (hi - lo) * rng.random(3)
-        if all(np.linalg.norm(c - p) >= min_sep for p in pts):
-            pts.append(c)
-    return np.array(pts)
+        if k == 0 or np.sqrt(((pts[:k] - c) ** 2).sum(axis=1)).min() >= min_sep:
+            pts[k] = c
+            k += 1
+    return pts
 
 
 def random_box(n: int, seed: int, box=(6.0, 6.0, 3.0), m: int = 100,
