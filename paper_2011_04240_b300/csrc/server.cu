@@ -332,8 +332,10 @@ void worker_main(amto_server_s* sv) {
                 size_t k = 0;
                 while (g.pre[k] < hi) ++k;
                 g.launched = g.pre[k];
-                if (cudaGraphLaunch(g.chunk[k], g.stream) != cudaSuccess) {
-                    set_error("server: chunk launch failed");
+                const cudaError_t ce = cudaGraphLaunch(g.chunk[k], g.stream);
+                if (ce != cudaSuccess) {
+                    set_error(std::string("server: chunk launch failed: ") +
+                              cudaGetErrorString(ce));
                     st = AMTO_ECUDA;
                 }
                 cudaMemcpyAsync(g.h_flags, g.plan->flags, 4 * (size_t)g.launched,
@@ -345,8 +347,10 @@ void worker_main(amto_server_s* sv) {
         for (auto& gp : sv->groups) {
             Group& g = *gp;
             if (st != AMTO_OK || g.active == 0) continue;
-            if (cudaEventSynchronize(g.done_ev) != cudaSuccess) {
-                set_error("server: device error during a chunk");
+            const cudaError_t ce = cudaEventSynchronize(g.done_ev);
+            if (ce != cudaSuccess) {
+                set_error(std::string("server: device error during a chunk: ") +
+                          cudaGetErrorString(ce));
                 st = AMTO_ECUDA;
                 break;
             }
@@ -500,6 +504,8 @@ amto_status amto_server_poll(amto_server sv, uint64_t ticket, int wait_ms, float
     }
     Result& r = it->second;
     if (r.status == AMTO_EPENDING) return AMTO_EPENDING;
+    if (r.status != AMTO_OK && r.status != AMTO_ENONFINITE && r.status != AMTO_ETIMEOUT)
+        set_error("server worker stopped: " + sv->worker_msg);
     if (info) {
         info->iters = r.iters;
         info->resid = r.resid;

@@ -180,3 +180,19 @@ def test_shell64_first_iterations():
     for i, p in enumerate(probs):
         st = oracle_solve(M, p, 1, mode="R3")
         assert rel_inf(xi[i].reshape(3, -1), st.xi) < XI_TOL
+
+
+def test_plans_created_in_any_order_keep_their_launch_limits():
+    """Kernel attributes (dynamic shared-memory caps) are process-wide: a
+    plan whose kernels need less shared memory, created later, must not
+    break an earlier plan that needs more (48 agents, then 64)."""
+    p48 = W.random_box(48, 11, box=(8.0, 8.0, 4.0))
+    p64 = W.random_box(64, 12, box=(8.0, 8.0, 4.0))
+    a = planner(p48, max_batch=2)
+    b = planner(p64, max_batch=2)
+    x48, r48, k48 = gpu_solve(a, [p48, p48], 2)
+    x64, r64, k64 = gpu_solve(b, [p64, p64], 2)
+    assert np.all(k48 == 2) and np.all(k64 == 2)
+    assert np.all(np.isfinite(r48)) and np.all(np.isfinite(r64))
+    st = oracle_solve(oracle_mats(p48), p48, 2)
+    assert rel_inf(x48[0].reshape(3, -1), st.xi) < 1e-4

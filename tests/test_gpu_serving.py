@@ -43,9 +43,12 @@ def _collect(sv, tickets):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
-def test_same_result_alone_and_in_mix(precision):
+@pytest.mark.parametrize("slots", [8, 20])
+def test_same_result_alone_and_in_mix(precision, slots):
+    """slots = 20: chunks launch over slot prefixes of 8, 16 or 20 as the
+    occupancy changes; the probe's result must not depend on which."""
     sizes = (8, 16, 24)
-    sv = _server(sizes, precision)
+    sv = _server(sizes, precision, max_slots=slots)
     try:
         probe = W.random_box(16, 4242, box=(8.0, 8.0, 4.0))
         alone = _collect(sv, [sv.submit(probe.start, probe.goal)])
