@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4}  # AMTO_PREC_*
 METRIC = "instance-iterations/s and p50/p99 solve latency vs plain FP32, same residual"
 UNIT = "instance-iterations/s"
 
@@ -41,7 +42,8 @@ def parse():
     ap.add_argument("--impl", default="amto", choices=["amto", "reference"])
     ap.add_argument("--batch", type=int, default=256, help="instances per GPU")
     ap.add_argument("--agents", type=int, default=64)
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "tf32"],
+    ap.add_argument("--precision", default="tf32x3",
+                    choices=["fp32", "tf32x3", "bf16x3", "tf32", "bf16"],
                     help="arithmetic of the cached-inverse apply (pair step is float32)")
     ap.add_argument("--trace", action="store_true",
                     help="run the timed solve from the host loop (no graph), as profilers need")
@@ -50,15 +52,28 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving sweep only: Poisson arrivals of mixed agent counts against "
                          "the continuous-batching server and the plain per-instance solve")
-    ap.add_argument("--rates", default="100,500,1000,2000,5000",
+    ap.add_argument("--precision-report", action="store_true",
+                    help="errors of every apply precision against the FP64 oracle on 4 "
+                         "sampled instances of the batch, at k = 1, 2, 5, 10, 20, 200")
+    ap.add_argument("--rates", default="100,200,500,1000,2000,5000",
                     help="arrival rates (req/s) of the serving sweep")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of each serving run")
     return ap.parse_args()
 
 
 SERVE_SIZES = (8, 16, 32, 48, 64)
-SERVE_TOL, SERVE_MAX_ITERS = 1e-2, 1000
+SERVE_TOL, SERVE_MAX_ITERS = 1e-2, 2000
+SERVE_POOL = 1000  # distinct problems per agent count; longer runs cycle through them
+_serve_pool = {}
+
+
+def serving_problem(n, problem_seed):
+    import workloads as W
+    key = (n, problem_seed % SERVE_POOL)
+    if key not in _serve_pool:
+        _serve_pool[key] = W.config5_problem(n, key[1] + 7919 * n)
+    return _serve_pool[key]
 
 
 def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
@@ -74,8 +89,11 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
     import workloads as W
     from paper_2011_04240_b300 import Planner, Server, amto
     from paper_2011_04240_b300 import serving as SV
-    prec = {"fp32": amto.PREC_FP32, "tf32x3": amto.PREC_TF32X3, "tf32": amto.PREC_TF32}[precision]
-    arr = [(t, p.start, p.goal) for t, p in W.config5_arrivals(rate, seconds, seed)]
+    prec = PRECISIONS[precision]
+    arr = []
+    for t, n, ps in W.config5_schedule(rate, seconds, seed, SERVE_SIZES):
+        p = serving_problem(n, ps)
+        arr.append((t, p.start, p.goal))
     warm = [W.random_box(n, 99991 + n, box=(8.0, 8.0, 4.0)) for n in SERVE_SIZES]
     sv = Server(SERVE_SIZES, m_steps=100, T=8.0, proj_mode=amto.PROJ_LITERAL, precision=prec,
                 max_slots=256, chunk_iters=8, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL)
@@ -85,11 +103,11 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
             while sv.poll(t, 1000) is None:
                 pass
         slots = sv.stats()["slots"]
-        recs, wall = SV.run_arrivals(sv, arr)
+        recs, wall = SV.run_arrivals(sv, arr, keep_xi=False)
     finally:
         sv.close()
-    out = {"rate_req_s": rate, "window_s": seconds,
-           "server": dict(SV.summarize(recs, wall), apply_precision=precision,
+    out = {"rate_req_s": rate, "window_s": seconds, "iteration_cap": SERVE_MAX_ITERS,
+           "server": dict(SV.summarize(recs, wall, SERVE_MAX_ITERS), apply_precision=precision,
                           slots={str(k): v for k, v in slots.items()})}
     planners = {n: Planner(n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, max_batch=1)
                 for n in SERVE_SIZES}
@@ -103,7 +121,7 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
     finally:
         for pl in planners.values():
             pl.close()
-    out["plain_fp32_per_instance"] = dict(SV.summarize(recs2, wall2),
+    out["plain_fp32_per_instance"] = dict(SV.summarize(recs2, wall2, SERVE_MAX_ITERS),
                                           note=f"first {len(sub)} of the same arrivals")
     return out
 
@@ -273,6 +291,72 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
             "iterations": its, "final_resid_max": max(res)}
 
 
+def precision_report(args, ks=(1, 2, 5, 10, 20, 200), samples=(0, 85, 170, 255)):
+    """xi error (max|xi - xi_oracle| / max|xi_oracle|) of each apply precision
+    on sampled instances of the batched workload, against the FP64 oracle
+    run on the same inputs, plus the oracle's own sensitivity horizon K_par
+    (largest k at which runs from inputs perturbed by 1e-7 relative noise
+    stay within 1e-4 of the unperturbed run) and the final max residual of
+    every precision at the last k."""
+    import numpy as np
+    import torch
+    import oracle as O
+    import workloads as W
+    from paper_2011_04240_b300 import Planner, amto
+    probs = workload(args, 0)
+    B, n = len(probs), probs[0].n
+    samples = [i for i in samples if i < B]
+    M = O.build_matrices(n, probs[0].m, probs[0].degree, probs[0].T, probs[0].a, probs[0].b,
+                         probs[0].rho)
+
+    def oracle_run(start, goal, kmax):
+        beq = O.boundary_values(start, goal)
+        st = O.init_state(M, beq, "R3")
+        snaps = {}
+        for k in range(1, kmax + 1):
+            st = O.am_iteration(M, st, beq, "R3")
+            if k in ks:
+                snaps[k] = st.xi.copy()
+        return snaps
+
+    t0 = time.perf_counter()
+    ref = {i: oracle_run(probs[i].start, probs[i].goal, max(ks)) for i in samples}
+    # sensitivity horizon of the problem itself, on the first sample
+    rng = np.random.default_rng(7)
+    p0 = probs[samples[0]]
+    kpar = max(ks)
+    for _ in range(3):
+        ps = (p0.start.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(p0.start.shape)))
+        pg = (p0.goal.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(p0.goal.shape)))
+        pert = oracle_run(ps, pg, max(ks))
+        for k in ks:
+            a, b = pert[k], ref[samples[0]][k]
+            if np.abs(a - b).max() / np.abs(b).max() > 1e-4:
+                kpar = min(kpar, [kk for kk in ks if kk < k][-1] if k > ks[0] else 0)
+                break
+    oracle_s = time.perf_counter() - t0
+    s_np, g_np = W.stack(probs)
+    s = torch.from_numpy(s_np).cuda()
+    g = torch.from_numpy(g_np).cuda()
+    out = {"workload": f"{B} x {n}-agent sphere shell, lambda-free projection",
+           "samples": samples, "k": list(ks), "oracle_K_par": kpar,
+           "oracle_seconds": oracle_s, "errors": {}, "final_resid_max": {}}
+    for name, prec in PRECISIONS.items():
+        pl = Planner(n, probs[0].m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho,
+                     probs[0].degree, proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
+        errs = {}
+        for k in ks:
+            xi, r, it = pl.solve(s, g, k)
+            x = xi.cpu().numpy()
+            errs[k] = max(float(np.abs(x[i].reshape(3, -1) - ref[i][k]).max()
+                                / np.abs(ref[i][k]).max()) for i in samples)
+            if k == max(ks):
+                out["final_resid_max"][name] = float(r.max().item())
+        out["errors"][name] = errs
+        pl.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
     if rank != 0:
@@ -324,16 +408,25 @@ def main():
     import torch
     import torch.distributed as dist
 
+    if args.precision_report:
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(precision_report(args)), flush=True)
+        return
+
     if args.serve:
         torch.cuda.set_device(local)
         import __graft_entry__
         __graft_entry__.build()
-        runs = [serving_compare(float(r), args.serve_seconds, args.precision)
-                for r in args.rates.split(",")]
+        runs = []
+        for r in args.rates.split(","):
+            runs.append(serving_compare(float(r), args.serve_seconds, args.precision))
+            print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
         print(json.dumps({"metric": "serving: p50/p99 latency and instance-iterations/s",
                           "workload": "Poisson arrivals, agent counts uniform in "
                                       "{8,16,32,48,64}, degree 10, m=100, 8x8x4 m box, "
-                                      "tol 1e-2", "runs": runs}), flush=True)
+                                      "tol 1e-2, iteration cap 2000", "runs": runs}), flush=True)
         return
 
     torch.cuda.set_device(local)
@@ -346,7 +439,7 @@ def main():
 
     probs = workload(args, rank)
     n, m, B, K = probs[0].n, probs[0].m, len(probs), args.steps
-    prec = {"fp32": amto.PREC_FP32, "tf32x3": amto.PREC_TF32X3, "tf32": amto.PREC_TF32}[args.precision]
+    prec = PRECISIONS[args.precision]
     pl = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
                  proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
     s_np, g_np = W.stack(probs)
@@ -433,7 +526,7 @@ def main():
                                                           "apply": kms[2] / max(kcnt[2], 1)}}
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
-            extras["serving"] = serving_compare(1000.0, 1.0, args.precision)
+            extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

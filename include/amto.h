@@ -62,10 +62,13 @@ enum {
  * in every mode. */
 enum {
     AMTO_PREC_FP32 = 0,     /* float32 SIMT */
-    AMTO_PREC_TF32X3 = 1,   /* tensor cores, hi/lo split, 3 products, fp32 accumulate */
-    AMTO_PREC_BF16X3 = 2,   /* tensor cores, hi/lo split, 3 products, fp32 accumulate */
-    AMTO_PREC_TF32 = 3,     /* tensor cores, single product */
-    AMTO_PREC_BF16 = 4      /* tensor cores, single product */
+    AMTO_PREC_TF32X3 = 1,   /* tensor cores (tcgen05 kind::tf32): operands split into a
+                               TF32 hi and a float32 lo part, 3 products (hi*hi + hi*lo +
+                               lo*hi), float32 accumulate; tracks float32 to ~1e-6 */
+    AMTO_PREC_BF16X3 = 2,   /* tensor cores (kind::f16, BF16 operands): BF16 hi and BF16
+                               lo parts, 3 products, float32 accumulate (~16 bits) */
+    AMTO_PREC_TF32 = 3,     /* tensor cores, TF32 operands, single product */
+    AMTO_PREC_BF16 = 4      /* tensor cores, BF16 operands, single product */
 };
 
 /* Boundary-condition bits (rows of A in Sec. III-B). */

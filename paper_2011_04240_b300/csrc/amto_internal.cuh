@@ -26,6 +26,10 @@ void clear_error();
         }                                                                          \
     } while (0)
 
+// Apply precisions that run on the tensor cores, and those with BF16 operands.
+inline bool prec_tc(int p) { return p != AMTO_PREC_FP32; }
+inline bool prec_bf16(int p) { return p == AMTO_PREC_BF16X3 || p == AMTO_PREC_BF16; }
+
 // Flags per instance (device int).
 enum : int { FLAG_DONE = 1, FLAG_APPLY = 2, FLAG_NONFINITE = 4 };
 
@@ -90,6 +94,9 @@ struct amto_plan_s {
     int kp = 0;                // padded row length (multiple of 4) of the tensor-core operands
     float* Kt_hi = nullptr;    // [n nv][kp] TF32-rounded K^-1_top (tensor-core modes)
     float* Kt_lo = nullptr;    // [n nv][kp] float32 residual K^-1_top - Kt_hi
+    int kp8 = 0;               // padded row length (multiple of 8) of the BF16 operands
+    unsigned short* Kb_hi = nullptr;  // [n nv][kp8] BF16(K^-1_top) (BF16 modes)
+    unsigned short* Kb_lo = nullptr;  // [n nv][kp8] BF16(K^-1_top - Kb_hi)
     CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;  // TMA descriptors (64-byte aligned type)
 
     // state for max_batch instances (device)
@@ -100,6 +107,8 @@ struct amto_plan_s {
     float* rpart = nullptr;    // [B][n_chunks]
     float* rhs = nullptr;      // [B][3][kp] (TF32-rounded in tensor-core modes)
     float* rhs_lo = nullptr;   // [B][3][kp] residual rhs - rhs (TF32X3 mode)
+    unsigned short* rb_hi = nullptr;  // [B][3][kp8] BF16(rhs) (BF16 modes)
+    unsigned short* rb_lo = nullptr;  // [B][3][kp8] BF16(rhs - rb_hi) (BF16X3 mode)
     float* rmax = nullptr;     // [B]
     unsigned long long* r64 = nullptr;  // [B] FP64 final residual^2 bits
     int* iters = nullptr;      // [B]

@@ -56,7 +56,7 @@ void free_plan(amto_plan_s* pl) {
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kinv64, pl->Ktop,
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
-                    pl->Kt_hi, pl->Kt_lo, pl->rhs_lo,
+                    pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
                     pl->gemm_tk, pl->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -171,9 +171,8 @@ amto_status validate_params(const amto_params& p) {
     if (nb >= p.poly_degree + 1) return einval("more boundary conditions than coefficients");
     if (p.proj_mode != AMTO_PROJ_LITERAL && p.proj_mode != AMTO_PROJ_NOLAMBDA)
         return einval("proj_mode");
-    if (p.precision != AMTO_PREC_FP32 && p.precision != AMTO_PREC_TF32X3 &&
-        p.precision != AMTO_PREC_TF32)
-        return einval("precision: AMTO_PREC_FP32, AMTO_PREC_TF32X3 and AMTO_PREC_TF32 are available");
+    if (p.precision < AMTO_PREC_FP32 || p.precision > AMTO_PREC_BF16)
+        return einval("precision must be one of AMTO_PREC_*");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
     return AMTO_OK;
 }
@@ -217,8 +216,9 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m);
-    pl->kp = (pl->kdim + 3) / 4 * 4;  // 16-byte rows for the tensor-memory-access descriptors
-    const bool tc = p.precision == AMTO_PREC_TF32X3 || p.precision == AMTO_PREC_TF32;
+    pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
+    pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
+    const bool tc = prec_tc(p.precision), bf = prec_bf16(p.precision);
     const int B = p.max_batch, n = pl->n, nv = pl->nv, kdim = pl->kdim;
     const size_t nvn = (size_t)n * nv;
 
@@ -237,10 +237,16 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->E0, (size_t)nv * nb);
     ALLOC(pl->Kinv64, (size_t)kdim * kdim);
     ALLOC(pl->Ktop, nvn * kdim);
-    if (tc) {
+    if (tc && !bf) {
         ALLOC(pl->Kt_hi, nvn * pl->kp);
         ALLOC(pl->Kt_lo, nvn * pl->kp);
         ALLOC(pl->rhs_lo, (size_t)B * 3 * pl->kp);
+    }
+    if (bf) {
+        ALLOC(pl->Kb_hi, nvn * pl->kp8);
+        ALLOC(pl->Kb_lo, nvn * pl->kp8);
+        ALLOC(pl->rb_hi, (size_t)B * 3 * pl->kp8);
+        ALLOC(pl->rb_lo, (size_t)B * 3 * pl->kp8);
     }
     ALLOC(pl->xi, (size_t)B * 3 * nvn);
     ALLOC(pl->beq, (size_t)B * 3 * n * nb);

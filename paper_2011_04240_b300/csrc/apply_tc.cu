@@ -7,13 +7,15 @@
 // One block computes a 128 x 128 output tile over a slice of K:
 //   warp 0 lane 0   TMA producer: 2-D tiled bulk-tensor loads (128-byte
 //                   swizzle) of the K^-1 tile and the right-hand-side tile,
-//                   each split into a TF32 "hi" part and a float32 residual
-//                   "lo" part, into a 3-stage shared-memory ring;
-//   warp 1 lane 0   MMA issuer: tcgen05.mma kind::tf32, accumulator in
+//                   each split into a "hi" part (TF32, or BF16) and the
+//                   residual "lo" part (float32, or BF16), into a 3-stage
+//                   shared-memory ring;
+//   warp 1 lane 0   MMA issuer: tcgen05.mma kind::tf32 (K = 8 per MMA) or
+//                   kind::f16 with BF16 operands (K = 16 per MMA; both are
+//                   32 bytes of a 128-byte swizzled row), accumulator in
 //                   tensor memory (128 lanes x 128 float32 columns), three
 //                   products per k-step (hi*hi + hi*lo + lo*hi, the split
-//                   ("x3") correction that recovers float32 accuracy), or one
-//                   (plain TF32);
+//                   ("x3") correction), or one (plain TF32 / BF16);
 //   all 4 warps     epilogue: tcgen05.ld of the accumulator, then either an
 //                   add into xi or a split-K partial (summed in split order
 //                   by the separate reduce kernel).
@@ -29,8 +31,9 @@
 namespace amto {
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 32, kTcStages = 3;
-constexpr int kTileBytes = kBM * kBK * 4;            // 16 KB (kBN == kBM)
+constexpr int kBM = 128, kBN = 128, kTcStages = 3;
+constexpr int kRowBytes = 128;                       // one swizzled K row of a tile
+constexpr int kTileBytes = kBM * kRowBytes;          // 16 KB (kBN == kBM)
 constexpr int kTcStageBytes = 4 * kTileBytes;       // A hi, A lo, B hi, B lo
 constexpr unsigned kTcPolls = 1u << 22;
 
@@ -76,16 +79,26 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr) {
     d |= (uint64_t)2 << 61;                            // 128-byte swizzle
     return d;
 }
-// Instruction descriptor: D float32, A and B TF32, both K-major, N x M tile.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+// Instruction descriptors: D float32, A and B both K-major, N x M tile;
+// operand format TF32 (kind::tf32) or BF16 (kind::f16).
+constexpr uint32_t kIdescShape = ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | kIdescShape;
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | kIdescShape;
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-        : "memory");
+template <bool BF>
+__device__ __forceinline__ void mma_step(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    if (BF)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(kIdescBf16), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(kIdescTf32), "r"(acc)
+            : "memory");
 }
 __device__ __forceinline__ void mma_commit(unsigned bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -108,6 +121,7 @@ struct TcArgs {
     Ctl* ctl;
 };
 
+template <bool BF>
 __global__ void __launch_bounds__(128, 1)
     k_apply_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
@@ -117,6 +131,7 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ unsigned tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, kz = blockIdx.z;
+    constexpr int kBK = BF ? kRowBytes / 2 : kRowBytes / 4;  // K elements per k-block
     const int kbeg = kz * A.kper, kend = min(A.K, kbeg + A.kper);
     const int nk = (kend - kbeg + kBK - 1) / kBK;
     const unsigned base = (su32(tc_smem) + 1023u) & ~1023u;  // 1024-byte aligned tiles
@@ -175,15 +190,15 @@ __global__ void __launch_bounds__(128, 1)
             tc_fence_after();
             const unsigned st = base + s * kTcStageBytes;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 8; ++kk) {  // K = 8 TF32 elements (32 bytes) per MMA
+            for (int kk = 0; kk < kRowBytes / 32; ++kk) {  // 32 bytes of K per MMA
                 const uint64_t ah = smem_desc(st + kk * 32);
                 const uint64_t bh = smem_desc(st + 2 * kTileBytes + kk * 32);
-                mma_tf32(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
+                mma_step<BF>(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
                 if (A.x3) {
                     const uint64_t al = smem_desc(st + kTileBytes + kk * 32);
                     const uint64_t bl = smem_desc(st + 3 * kTileBytes + kk * 32);
-                    mma_tf32(tmem, ah, bl, 1u);
-                    mma_tf32(tmem, al, bh, 1u);
+                    mma_step<BF>(tmem, ah, bl, 1u);
+                    mma_step<BF>(tmem, al, bh, 1u);
                 }
             }
             mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
@@ -257,19 +272,21 @@ EncodeTiled encoder() {
     return fn;
 }
 
-// Row-major float32 matrix [rows][ld] with `cols` valid columns: 32 x 128
-// boxes, 128-byte swizzle, zero fill outside.
-amto_status make_map(CUtensorMap* map, const float* base, int rows, int cols, int ld) {
+// Row-major matrix [rows][ld] of float32 (or BF16) with `cols` valid columns:
+// 128-byte x 128-row boxes, 128-byte swizzle, zero fill outside.
+amto_status make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, bool bf16) {
+    const int es = bf16 ? 2 : 4;
     EncodeTiled enc = encoder();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
         return AMTO_ECUDA;
     }
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / es), (cuuint32_t)kBM};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+    CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -283,18 +300,31 @@ amto_status make_map(CUtensorMap* map, const float* base, int rows, int cols, in
 size_t tc_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + 1024; }
 
 amto_status tc_configure(amto_plan_s* pl) {
-    AMTO_CUDA_TRY(cudaFuncSetAttribute((void*)k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AMTO_CUDA_TRY(cudaFuncSetAttribute((void*)k_apply_tc<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes()));
+    AMTO_CUDA_TRY(cudaFuncSetAttribute((void*)k_apply_tc<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes()));
     const int M = pl->n * pl->nv, K = pl->kdim, rows_b = 3 * pl->prm.max_batch;
-    amto_status st = make_map(&pl->tm_a_hi, pl->Kt_hi, M, K, pl->kp);
-    if (st == AMTO_OK) st = make_map(&pl->tm_a_lo, pl->Kt_lo, M, K, pl->kp);
-    if (st == AMTO_OK) st = make_map(&pl->tm_b_hi, pl->rhs, rows_b, K, pl->kp);
-    if (st == AMTO_OK) st = make_map(&pl->tm_b_lo, pl->rhs_lo, rows_b, K, pl->kp);
+    amto_status st;
+    if (prec_bf16(pl->prm.precision)) {
+        st = make_map(&pl->tm_a_hi, pl->Kb_hi, M, K, pl->kp8, true);
+        if (st == AMTO_OK) st = make_map(&pl->tm_a_lo, pl->Kb_lo, M, K, pl->kp8, true);
+        if (st == AMTO_OK) st = make_map(&pl->tm_b_hi, pl->rb_hi, rows_b, K, pl->kp8, true);
+        if (st == AMTO_OK) st = make_map(&pl->tm_b_lo, pl->rb_lo, rows_b, K, pl->kp8, true);
+    } else {
+        st = make_map(&pl->tm_a_hi, pl->Kt_hi, M, K, pl->kp, false);
+        if (st == AMTO_OK) st = make_map(&pl->tm_a_lo, pl->Kt_lo, M, K, pl->kp, false);
+        if (st == AMTO_OK) st = make_map(&pl->tm_b_hi, pl->rhs, rows_b, K, pl->kp, false);
+        if (st == AMTO_OK) st = make_map(&pl->tm_b_lo, pl->rhs_lo, rows_b, K, pl->kp, false);
+    }
     return st;
 }
 
 void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, int* kper) {
     const int M = pl->n * pl->nv, N = 3 * batch, K = pl->kdim;
+    const int kbk = prec_bf16(pl->prm.precision) ? kRowBytes / 2 : kRowBytes / 4;
     *tm = (M + kBM - 1) / kBM;
     *tn = (N + kBN - 1) / kBN;
     // the split over K is fixed by the plan's largest batch, so a column's
@@ -303,7 +333,7 @@ void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, i
     int sp = pl->num_sms / (*tm * tn_max);  // one wave of one-block-per-SM tiles
     sp = sp < 1 ? 1 : (sp > 8 ? 8 : sp);
     int kp = (K + sp - 1) / sp;
-    kp = (kp + kBK - 1) / kBK * kBK;
+    kp = (kp + kbk - 1) / kbk * kbk;
     *splits = (K + kp - 1) / kp;
     *kper = kp;
 }
@@ -313,7 +343,7 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     a.M = pl->n * pl->nv;
     a.K = pl->kdim;
     a.N = 3 * batch;
-    a.x3 = pl->prm.precision == AMTO_PREC_TF32X3;
+    a.x3 = pl->prm.precision == AMTO_PREC_TF32X3 || pl->prm.precision == AMTO_PREC_BF16X3;
     a.xi = pl->xi;
     a.flags = pl->flags;
     a.ws = pl->gemm_ws;
@@ -321,8 +351,12 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     int tm, tn, sp;
     tc_shape(pl, batch, &tm, &tn, &sp, &a.kper);
     a.splits = sp;
-    k_apply_tc<<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(pl->tm_a_hi, pl->tm_a_lo,
-                                                              pl->tm_b_hi, pl->tm_b_lo, a);
+    if (prec_bf16(pl->prm.precision))
+        k_apply_tc<true><<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(
+            pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a);
+    else
+        k_apply_tc<false><<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(
+            pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a);
     AMTO_CUDA_TRY(cudaGetLastError());
     if (sp > 1) return launch_splitk_reduce(pl, batch, sp, s);
     return AMTO_OK;

@@ -11,6 +11,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "amto_internal.cuh"
 
 namespace amto {
@@ -230,6 +232,18 @@ __global__ void k_split_top(int rows, int kdim, int ld, const double* Kinv, floa
     lo[idx] = (float)(x - (double)h);
 }
 
+// BF16 split of the top rows of K^-1: hi = BF16(K^-1), lo = BF16(K^-1 - hi).
+__global__ void k_split_top_bf16(int rows, int kdim, int ld, const double* Kinv,
+                                 __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)rows * ld) return;
+    int r = (int)(idx / ld), c = (int)(idx % ld);
+    double x = (c < kdim) ? Kinv[(long long)r * kdim + c] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+}
+
 // E0 = rows [0, nv) and columns [nv, nv+nb) of the agent-level inverse.
 __global__ void k_extract_e0(int nv, int nb, const double* K0inv, float* E0) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -341,6 +355,10 @@ amto_status precompute(amto_plan_s* pl) {
         if (pl->Kt_hi)
             k_split_top<<<blocks((long long)rows * pl->kp, 256), 256, 0, s>>>(
                 rows, kdim, pl->kp, pl->Kinv64, pl->Kt_hi, pl->Kt_lo);
+        if (pl->Kb_hi)
+            k_split_top_bf16<<<blocks((long long)rows * pl->kp8, 256), 256, 0, s>>>(
+                rows, kdim, pl->kp8, pl->Kinv64, reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi),
+                reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo));
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);

@@ -47,7 +47,10 @@ size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision)
     b += 2 * 4 * (size_t)g.lam_floats;         // multipliers (two buffers)
     b += 4 * (size_t)g.n_chunks * 3 * nvn;     // unit partials
     b += 4 * (size_t)g.n_chunks;
-    b += 4 * 3 * kp * (precision == AMTO_PREC_FP32 ? 1 : 2);  // right-hand side(s)
+    const size_t kp8 = (kdim + 7) / 8 * 8;
+    b += 4 * 3 * kp;                                            // right-hand side
+    if (precision == AMTO_PREC_TF32X3 || precision == AMTO_PREC_TF32) b += 4 * 3 * kp;
+    if (prec_bf16(precision)) b += 2 * 2 * 3 * kp8;             // BF16 hi / lo copies
     b += 4 * 8 * 3 * nvn;                      // split-K workspace share
     b += 32;                                   // flags, counters
     return b;

@@ -18,7 +18,7 @@ import numpy as np
 from . import amto
 
 
-def summarize(records, wall_s):
+def summarize(records, wall_s, cap=None):
     """p50/p99 latency (ms), throughput (instance-iterations/s, requests/s)
     and the residual spread of a list of request records."""
     lat = np.array([r["latency"] for r in records], dtype=np.float64) * 1e3
@@ -33,10 +33,11 @@ def summarize(records, wall_s):
         "mean_iters": float(its.mean()) if len(its) else None,
         "resid_max": float(res.max()) if len(res) else None,
         "resid_p50": float(np.median(res)) if len(res) else None,
+        "frac_at_cap": float((its >= cap).mean()) if (cap and len(its)) else None,
     }
 
 
-def run_arrivals(server: "amto.Server", arrivals, wait_ms: int = 1000):
+def run_arrivals(server: "amto.Server", arrivals, wait_ms: int = 1000, keep_xi: bool = True):
     """Submit each (t_s, start, goal) of ``arrivals`` (sorted by t_s) at its
     arrival time, relative to the call; collect every result.
 
@@ -68,6 +69,8 @@ def run_arrivals(server: "amto.Server", arrivals, wait_ms: int = 1000):
                 res = server.poll(ticket, wait_ms)
             res["n"] = n
             res["latency"] = res["t_done"] - res["t_submit"]
+            if not keep_xi:
+                del res["xi"]
             records.append(res)
             i += 1
 

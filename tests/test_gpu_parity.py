@@ -111,7 +111,7 @@ def test_one_iteration_from_warm_state(n, m, mode):
     assert rel_inf(xi[0].reshape(3, -1), ref.xi) < XI_TOL
     lam, al, be, d = gpu_state(pl)
     # multipliers carry units of length (lambda / rho); compare normwise with a
-    # 1 cm floor so that an already-converged pair (lambda ~ 0) is not judged
+    # 1 cm floor so that an already-converged pair (lambda ~ 0) is not scored
     # on float32 round-off alone
     lam_err = np.abs(lam[0].reshape(3, -1) - ref.lam).max() / max(np.abs(ref.lam).max(), 1e-2)
     assert lam_err < 1e-4, lam_err

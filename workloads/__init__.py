@@ -153,9 +153,9 @@ def config4(n_instances: int = 256, seed: int = 0, n: int = 64) -> list[Problem]
             for i in range(n_instances)]
 
 
-def config5_arrivals(rate: float, duration_s: float, seed: int = 0,
+def config5_schedule(rate: float, duration_s: float, seed: int = 0,
                      sizes=(8, 16, 32, 48, 64)):
-    """Poisson arrivals: list of (arrival_time_s, Problem) in an 8x8x4 m box."""
+    """Poisson arrival times with agent counts: list of (t_s, n, problem_seed)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -165,10 +165,21 @@ def config5_arrivals(rate: float, duration_s: float, seed: int = 0,
         if t > duration_s:
             break
         n = int(rng.choice(np.asarray(sizes)))
-        out.append((t, random_box(n, seed * 1000003 + i, box=(8.0, 8.0, 4.0),
-                                  m=100, T=8.0)))
+        out.append((t, n, seed * 1000003 + i))
         i += 1
     return out
+
+
+def config5_problem(n: int, problem_seed: int) -> Problem:
+    """One serving request: random 8x8x4 m box, m = 100, T = 8 s."""
+    return random_box(n, problem_seed, box=(8.0, 8.0, 4.0), m=100, T=8.0)
+
+
+def config5_arrivals(rate: float, duration_s: float, seed: int = 0,
+                     sizes=(8, 16, 32, 48, 64)):
+    """Poisson arrivals: list of (arrival_time_s, Problem) in an 8x8x4 m box."""
+    return [(t, config5_problem(n, ps)) for t, n, ps in
+            config5_schedule(rate, duration_s, seed, sizes)]
 
 
 def stack(problems: list[Problem]):
