@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving sweep only: Poisson arrivals of mixed agent counts against "
                          "the continuous-batching server and the plain per-instance solve")
+    ap.add_argument("--mixed", action="store_true",
+                    help="uneven batch only: 512 instances with agent counts uniform in "
+                         "{8,16,24,32}, one loop over all counts (fused pair launch)")
     ap.add_argument("--precision-report", action="store_true",
                     help="errors of every apply precision against the FP64 oracle on 4 "
                          "sampled instances of the batch, at k = 1, 2, 5, 10, 20, 200")
@@ -291,6 +294,92 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
             "iterations": its, "final_resid_max": max(res)}
 
 
+def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32"):
+    """Uneven batch: `n_instances` random 8x8x4 m boxes with agent counts drawn
+    uniformly from `sizes` (degree 10, m = 100, T = 8 s, literal projection),
+    K fixed iterations.  Timed three ways on device-resident inputs: one mixed
+    solve (all counts in one loop), the per-count solves one after another, and
+    the per-count solves on one stream each."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Mixed, Planner, amto
+    probs = W.config3(n_instances, seed=0, sizes=sizes)
+    by_n = {n: [p for p in probs if p.n == n] for n in sizes}
+    groups = [by_n[n] for n in sizes if by_n[n]]
+    pls = [Planner(gr[0].n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, precision=PRECISIONS[prec],
+                   max_batch=len(gr)) for gr in groups]
+    starts, goals = [], []
+    for gr in groups:
+        s_np, g_np = W.stack(gr)
+        starts.append(torch.from_numpy(s_np).cuda())
+        goals.append(torch.from_numpy(g_np).cuda())
+    mx = Mixed(pls)
+    K, Wm = args.steps, max(args.warmup, 3)
+    outs = mx.solve(starts, goals, Wm)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    if args.trace:
+        mx.set_trace(True)
+    with ClockSampler(0) as clk:
+        ms_mixed = timed(lambda: mx.solve(starts, goals, K, out=outs))
+    its = sum(int(o[2].sum().item()) for o in outs)
+    assert its == n_instances * K, (its, n_instances * K)
+    if args.trace:
+        mx.set_trace(False)
+        mx.close()
+        return {"trace": True, "ms_per_step": ms_mixed / K}
+    for pl, gr in zip(pls, groups):  # per-count graphs and warm-up
+        pl.solve(starts[pls.index(pl)], goals[pls.index(pl)], Wm)
+    torch.cuda.synchronize()
+    ms_seq = timed(lambda: [pl.solve(starts[i], goals[i], K) for i, pl in enumerate(pls)])
+    streams = [torch.cuda.Stream() for _ in pls]
+
+    def concurrent():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        done = []
+        for i, pl in enumerate(pls):
+            streams[i].wait_event(ev)
+            pl.solve(starts[i], goals[i], K, stream=streams[i])
+            e = torch.cuda.Event()
+            e.record(streams[i])
+            done.append(e)
+        for e in done:
+            stream.wait_event(e)
+    ms_conc = timed(concurrent)
+    alg = sum(algorithmic_pair_bytes(gr[0].n, 100, len(gr)) for gr in groups)
+    hbm, src = peaks()
+    out = {"metric": "instance-iterations/s (uneven batch)", "unit": UNIT,
+           "workload": f"{n_instances} random 8x8x4 m boxes, agent counts uniform in "
+                       f"{list(sizes)} ({[len(g) for g in groups]} per count), degree 10, "
+                       "m=100, T=8 s, literal projection, fixed iterations",
+           "apply_precision": prec, "steps": K,
+           "mixed": {"value": n_instances * K / (ms_mixed / 1e3), "ms_per_step": ms_mixed / K},
+           "per_count_sequential": {"value": n_instances * K / (ms_seq / 1e3),
+                                    "ms_per_step": ms_seq / K},
+           "per_count_concurrent_streams": {"value": n_instances * K / (ms_conc / 1e3),
+                                            "ms_per_step": ms_conc / K},
+           "pair_algorithmic_bytes_per_step": alg,
+           "whole_step_gbs_mixed": alg / (ms_mixed / K / 1e3) / 1e9,
+           "hbm_peak_gbs": hbm, "peak_source": src, "clocks": clk.summary(),
+           "l2": f"multiplier state {sum(2 * p.info.lambda_floats * 4 * len(g) for p, g in zip(pls, groups)) / 1e6:.0f} MB"}
+    mx.close()
+    for pl in pls:
+        pl.close()
+    return out
+
+
 def precision_report(args, ks=(1, 2, 5, 10, 20, 200), samples=(0, 85, 170, 255)):
     """xi error (max|xi - xi_oracle| / max|xi_oracle|) of each apply precision
     on sampled instances of the batched workload, against the FP64 oracle
@@ -407,6 +496,13 @@ def main():
     import numpy as np
     import torch
     import torch.distributed as dist
+
+    if args.mixed:
+        torch.cuda.set_device(local)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(mixed_batch(args)), flush=True)
+        return
 
     if args.precision_report:
         torch.cuda.set_device(local)

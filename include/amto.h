@@ -90,7 +90,22 @@ typedef struct {
     int proj_mode;     /* AMTO_PROJ_* */
     int precision;     /* AMTO_PREC_* */
     int max_batch;     /* largest batch a solve may take, >= 1 */
+    /* Pair-kernel tiling (results do not depend on it; amto_tune measures):
+     * agents per lane group (0 = automatic, else 8, 16 or 32) and time blocks
+     * per warp and work unit (0 = automatic, else 1..8). */
+    int tile_group;
+    int tile_time_blocks;
+    int apply_mode;    /* AMTO_APPLY_*: where the cached inverse is applied */
 } amto_params;
+
+/* Where the step xi += K^-1_top [g; e] runs.  BATCHED: a separate right-hand-
+ * side launch and one GEMM launch over the batch per iteration (tensor cores
+ * in the TF32/BF16 modes).  FUSED (float32 only): the last block of each
+ * instance's pair step forms its right-hand side and applies K^-1 as a
+ * matrix-vector product (K^-1 read from L2), so an iteration is one launch.
+ * AUTO: BATCHED (faster on B300 at every size measured; amto_tune measures
+ * both). */
+enum { AMTO_APPLY_AUTO = 0, AMTO_APPLY_BATCHED = 1, AMTO_APPLY_FUSED = 2 };
 
 typedef struct {
     int n_agents, m_steps, nv, nb;      /* nv = N+1 coefficients, nb = #BC rows */
@@ -106,6 +121,8 @@ typedef struct {
                                            pair step */
     int launches_fixed;                 /* kernels per solve outside the loop: setup,
                                            initial projection, FP64 residual, outputs */
+    int time_blocks;                    /* pair-kernel time blocks per warp and unit */
+    int apply_mode;                     /* AMTO_APPLY_BATCHED or AMTO_APPLY_FUSED */
 } amto_info;
 
 /*
@@ -233,6 +250,84 @@ amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count);
  * Results are identical in both modes.
  */
 amto_status amto_set_trace(amto_plan plan, int on);
+
+/* ------------------------------------------------------------------------
+ * Autotuning of the pair-kernel tile (the library's own; the paper has no
+ * counterpart).  The tile (tile_group, tile_time_blocks of amto_params)
+ * changes which lanes and blocks process which pairs and samples, never a
+ * result.
+ * ------------------------------------------------------------------------ */
+#define AMTO_TUNE_MAX 32
+
+typedef struct {
+    int tile_group;            /* agents per lane group: 8, 16 or 32 */
+    int tile_time_blocks;      /* time blocks per warp and work unit */
+    int apply_mode;            /* AMTO_APPLY_BATCHED or AMTO_APPLY_FUSED */
+    double us_per_iteration;   /* measured loop time per iteration of the batch */
+} amto_tune_entry;
+
+typedef struct {
+    int n_entries;
+    amto_tune_entry entries[AMTO_TUNE_MAX];  /* every candidate measured, in order */
+    int best;                                /* index of the fastest entry */
+} amto_tune_result;
+
+/* Measure every tile (and, for float32 plans, both apply modes) that fits
+ * `params` (its tile and apply_mode fields are ignored) on a
+ * synthetic batch of `batch` instances (agents on a ring, antipodal goals),
+ * `iters` fixed iterations each: a plan per candidate is created, solved
+ * twice (2 and 2 + iters iterations, the difference is the loop time) and
+ * destroyed.  Synchronous; uses the current device.  Copy the best entry's
+ * three fields into amto_params before amto_create.
+ * Errors: EINVAL (bad params, 1 <= batch <= max_batch, 1 <= iters <= 1e5),
+ * ENOMEM, ECUDA. */
+amto_status amto_tune(const amto_params* params, int batch, int iters, amto_tune_result* out);
+
+/* ------------------------------------------------------------------------
+ * Mixed batches: instances with different agent counts iterated as one loop.
+ *
+ * The paper solves one problem (one agent count) at a time; grouping several
+ * plans is the library's own.  Every plan keeps its cached inverse (Remarks
+ * 1-2: it depends on the agent count only) and its state for up to max_batch
+ * instances.  Per iteration one launch forms the right-hand sides of all
+ * instances, one launch runs the cached-inverse GEMM tiles of all FP32 plans
+ * (tensor-core plans run their own apply), and one persistent launch runs the
+ * pair step (Algorithm 1's projection, multiplier update and A_fc^T
+ * reduction) for the (instance, time-chunk) units of all plans; the loop is a
+ * CUDA graph under a conditional WHILE node (built once per combination of
+ * batch sizes), stopping when no instance of any plan is still iterating.
+ * Per instance the result is that of amto_solve on its own plan (same
+ * arithmetic; only the launches are shared).
+ * ------------------------------------------------------------------------ */
+#define AMTO_MAX_MIXED_GROUPS 8
+
+typedef struct amto_mixed_s* amto_mixed;
+
+/* Group n_plans (1..AMTO_MAX_MIXED_GROUPS) distinct plans that agree on
+ * device, m_steps, poly_degree, T, a, b, rho, bc_mask and proj_mode.  The
+ * plans must outlive the mixed object, and a plan must not be solved by
+ * another call while a mixed solve that uses it is in flight.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+amto_status amto_mixed_create(const amto_plan* plans, int n_plans, amto_mixed* out);
+
+/* Solve batch[g] instances with plan g, for every g, as one loop; arguments
+ * per group are as in amto_solve (all six boundary conditions from start and
+ * goal with zero end velocities and accelerations, no warm start):
+ *   batch      host [n_plans], 1 <= batch[g] <= max_batch of plan g
+ *   start[g], goal[g]  device [batch[g]][n_g][3]   (host arrays of pointers)
+ *   xi_out[g]  device [batch[g]][3][n_g][N+1]; resid_out[g], iters_out[g]
+ *              device [batch[g]] (the arrays or entries may be NULL)
+ * Asynchronous on `stream`.  Errors: EINVAL, ECUDA. */
+amto_status amto_mixed_solve(amto_mixed mixed, const int* batch, const float* const* start,
+                             const float* const* goal, int max_iters, float tol,
+                             float* const* xi_out, float* const* resid_out,
+                             int* const* iters_out, void* stream);
+
+/* 1: run the loop from the host, one launch at a time (what profilers need;
+ * identical results), 0: the graph loop (default). */
+amto_status amto_mixed_set_trace(amto_mixed mixed, int on);
+
+void amto_mixed_destroy(amto_mixed mixed);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of requests of mixed agent counts.

@@ -4,4 +4,4 @@ The solver lives in libamto.so (CUDA, sm_103a) behind the C ABI of
 include/amto.h; `amto` is its ctypes binding.
 """
 from . import amto  # noqa: F401
-from .amto import AmtoError, Planner, Server  # noqa: F401
+from .amto import AmtoError, Mixed, Planner, Server  # noqa: F401

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libamto.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
+APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED = range(3)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
 STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",
@@ -37,7 +38,9 @@ class Params(ctypes.Structure):
                 ("poly_degree", ctypes.c_int), ("T", ctypes.c_double),
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("rho", ctypes.c_double),
                 ("bc_mask", ctypes.c_uint), ("proj_mode", ctypes.c_int),
-                ("precision", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
+                ("apply_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -46,7 +49,8 @@ class Info(ctypes.Structure):
                 ("t_chunk", ctypes.c_int), ("n_chunks", ctypes.c_int),
                 ("lambda_floats", ctypes.c_longlong), ("kkt_check", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
-                ("launches_fixed", ctypes.c_int)]
+                ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
+                ("apply_mode", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -76,6 +80,15 @@ class ServerStats(ctypes.Structure):
                 ("sizes", ctypes.c_int * 32), ("slots", ctypes.c_int * 32)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
+                ("apply_mode", ctypes.c_int), ("us_per_iteration", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_entries", ctypes.c_int), ("entries", TuneEntry * 32), ("best", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 SIGNATURES = {
     "amto_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
@@ -90,6 +103,15 @@ SIGNATURES = {
     "amto_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int)]),
     "amto_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
+    "amto_tune": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(TuneResult)]),
+    "amto_mixed_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "amto_mixed_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
+                                        ctypes.POINTER(_P), ctypes.c_int, ctypes.c_float,
+                                        ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                        ctypes.POINTER(_P), _P]),
+    "amto_mixed_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
+    "amto_mixed_destroy": (None, [_P]),
     "amto_server_create": (ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_P)]),
     "amto_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request),
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -188,6 +210,17 @@ def set_trace(plan, on: bool) -> None:
     _check(load().amto_set_trace(plan, 1 if on else 0))
 
 
+def tune(params: Params, batch: int, iters: int = 20) -> dict:
+    """Measure the pair-kernel tiles (and apply modes) for `params` on a
+    synthetic batch; returns {"best": (tile_group, tile_time_blocks,
+    apply_mode), "entries": [(G, QW, apply_mode, us/iteration)]}."""
+    r = TuneResult()
+    _check(load().amto_tune(ctypes.byref(params), int(batch), int(iters), ctypes.byref(r)))
+    ent = [(r.entries[i].tile_group, r.entries[i].tile_time_blocks, r.entries[i].apply_mode,
+            r.entries[i].us_per_iteration) for i in range(r.n_entries)]
+    return {"best": ent[r.best][:3], "entries": ent}
+
+
 def last_error() -> str:
     return load().amto_last_error().decode()
 
@@ -210,12 +243,14 @@ class Planner:
     def __init__(self, n_agents: int, m_steps: int, T: float, a: float = 0.6, b: float = 1.2,
                  rho: float = 1.0, poly_degree: int = 10, bc_mask: int = BC_ALL,
                  proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
-                 max_batch: int = 1):
+                 max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
+                 apply_mode: int = 0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
-                             proj_mode, precision, max_batch)
+                             proj_mode, precision, max_batch, tile_group, tile_time_blocks,
+                             apply_mode)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)
@@ -294,6 +329,68 @@ class Planner:
 
     def stats(self):
         return get_stats(self.plan)
+
+
+# ----------------------------------------------------------------------------
+# Mixed batches (several agent counts iterated as one loop)
+# ----------------------------------------------------------------------------
+
+class Mixed:
+    """Solve instances of several agent counts as one loop (amto_mixed_*).
+
+    `planners` are Planner objects (distinct agent counts, same m, degree,
+    T, a, b, rho, boundary mask and projection mode); they must outlive this
+    object.  solve() takes one (start, goal) pair of CUDA tensors per planner
+    ([B_g, n_g, 3] each) and returns one (xi, resid, iters) per planner.
+    """
+
+    def __init__(self, planners):
+        import torch
+        self._torch = torch
+        self.planners = list(planners)
+        arr = (_P * len(self.planners))(*[p.plan for p in self.planners])
+        h = _P()
+        _check(load().amto_mixed_create(arr, len(self.planners), ctypes.byref(h)))
+        self.handle = h.value
+
+    def solve(self, starts, goals, max_iters: int, tol: float = 0.0, out=None, stream=None):
+        torch = self._torch
+        ng = len(self.planners)
+        bs, outs = [], []
+        for g, pl in enumerate(self.planners):
+            B = starts[g].shape[0]
+            pl._check_tensor(starts[g], (B, pl.n, 3), "start")
+            pl._check_tensor(goals[g], (B, pl.n, 3), "goal")
+            bs.append(B)
+            if out is None:
+                outs.append((torch.empty((B, 3, pl.n, pl.nv), device=pl.device),
+                             torch.empty((B,), device=pl.device),
+                             torch.empty((B,), device=pl.device, dtype=torch.int32)))
+            else:
+                outs.append(out[g])
+        P = lambda xs: (_P * ng)(*[x.data_ptr() for x in xs])  # noqa: E731
+        s = stream if stream is not None else torch.cuda.current_stream(self.planners[0].device)
+        _check(load().amto_mixed_solve(self.handle, (ctypes.c_int * ng)(*bs), P(starts), P(goals),
+                                       int(max_iters), float(tol), P([o[0] for o in outs]),
+                                       P([o[1] for o in outs]), P([o[2] for o in outs]),
+                                       s.cuda_stream))
+        for pl, B in zip(self.planners, bs):
+            pl.last_batch = B
+        return outs
+
+    def set_trace(self, on: bool):
+        _check(load().amto_mixed_set_trace(self.handle, 1 if on else 0))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().amto_mixed_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------------------

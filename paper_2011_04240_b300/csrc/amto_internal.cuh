@@ -64,7 +64,9 @@ struct PairGeom {
     int grid;       // persistent pair-kernel blocks (set when the kernels are configured)
 };
 
-PairGeom choose_geometry(int n, int m);
+// Pair-kernel geometry for n agents and m samples: lane group G (0: the one
+// with the least padding) and time blocks per warp and unit QW (0: automatic).
+PairGeom choose_geometry(int n, int m, int G_req = 0, int QW_req = 0);
 
 struct Graph {
     cudaGraph_t graph = nullptr;
@@ -120,6 +122,7 @@ struct amto_plan_s {
     amto::Ctl* ctl_host = nullptr;   // pinned mirror for host polling
 
     int last_batch = 0;
+    bool fused = false;        // K^-1 applied per instance inside the pair kernel
     cudaStream_t cap_stream = nullptr;
     std::map<int, amto::Graph> graphs;
 
@@ -131,6 +134,11 @@ struct amto_plan_s {
 
 namespace amto {
 // precompute.cu
+// Dynamic shared memory of the pair kernel for a tile (n agents, nv
+// coefficients, nb boundary rows, TC samples per unit, npad padded agents).
+size_t pair_smem_bytes_host(int n, int nv, int nb, int TC, int npad, bool fused);
+// Whether a plan with these parameters applies K^-1 inside the pair kernel.
+bool apply_fused(const amto_params& p);
 // Checks of amto_params (no CUDA call); sets the error text on failure.
 amto_status validate_params(const amto_params& p);
 amto_status precompute(amto_plan_s* pl);
@@ -153,6 +161,14 @@ amto_status launch_splitk_reduce(amto_plan_s* pl, int batch, int splits, cudaStr
 // apply_tc.cu (tensor-core apply)
 size_t tc_smem_bytes();
 amto_status tc_configure(amto_plan_s* pl);
+// Mixed batches (several plans iterated as one loop; csrc/mixed.cu).
+amto_status launch_ctl_reset(Ctl* ctl, int max_iters, float tol, cudaStream_t s);
+amto_status launch_rhs_mixed(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
+amto_status launch_apply_mixed(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
+amto_status configure_pair_mixed(amto_plan_s* const* pls, int ng, int* grid);
+amto_status launch_pair_mixed(amto_plan_s* const* pls, const int* batch, int ng, Ctl* ctl,
+                              int grid, cudaGraphConditionalHandle h, int use_cond,
+                              cudaStream_t s);
 // Tile grid, split-K count and K per split of the tensor-core apply.
 void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, int* kper);
 // Kernel launches of one iteration of a batch-`batch` solve.

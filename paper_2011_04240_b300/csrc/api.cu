@@ -174,6 +174,21 @@ amto_status validate_params(const amto_params& p) {
     if (p.precision < AMTO_PREC_FP32 || p.precision > AMTO_PREC_BF16)
         return einval("precision must be one of AMTO_PREC_*");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
+    if (p.apply_mode < AMTO_APPLY_AUTO || p.apply_mode > AMTO_APPLY_FUSED)
+        return einval("apply_mode must be one of AMTO_APPLY_*");
+    if (p.apply_mode == AMTO_APPLY_FUSED && p.precision != AMTO_PREC_FP32)
+        return einval("the fused apply is float32 (AMTO_PREC_FP32) only");
+    if (p.tile_group != 0 && p.tile_group != 8 && p.tile_group != 16 && p.tile_group != 32)
+        return einval("tile_group must be 0 (automatic), 8, 16 or 32");
+    if (p.tile_time_blocks < 0 || p.tile_time_blocks > 8)
+        return einval("tile_time_blocks must be in [0, 8]");
+    {
+        const PairGeom g = choose_geometry(p.n_agents, p.m_steps, p.tile_group, p.tile_time_blocks);
+        if (pair_smem_bytes_host(p.n_agents, p.poly_degree + 1, __builtin_popcount(p.bc_mask),
+                                 g.TC, g.npad, apply_fused(p)) > 227 * 1024)
+            return einval("the pair-kernel tile does not fit in shared memory; use fewer "
+                          "time blocks per warp");
+    }
     return AMTO_OK;
 }
 
@@ -215,7 +230,8 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->nb = nb;
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
-    pl->geo = choose_geometry(pl->n, pl->m);
+    pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks);
+    pl->fused = apply_fused(p);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
     pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
     const bool tc = prec_tc(p.precision), bf = prec_bf16(p.precision);
@@ -373,6 +389,8 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->device_bytes = plan->bytes;
     out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
     out->launches_fixed = 4;
+    out->time_blocks = plan->geo.QW;
+    out->apply_mode = plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
     return AMTO_OK;
 }
 

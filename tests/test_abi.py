@@ -54,7 +54,11 @@ def _params(**kw):
                                  dict(poly_degree=1), dict(T=0.0), dict(a=-1.0),
                                  dict(b=float("nan")), dict(rho=0.0), dict(bc_mask=0b001000),
                                  dict(bc_mask=64 | 63), dict(proj_mode=7), dict(max_batch=0),
-                                 dict(precision=9)])
+                                 dict(precision=9), dict(tile_group=12), dict(tile_group=4),
+                                 dict(tile_time_blocks=-1), dict(tile_time_blocks=9),
+                                 dict(n_agents=256, tile_group=8, tile_time_blocks=8),
+                                 dict(apply_mode=3), dict(apply_mode=-1),
+                                 dict(apply_mode=2, precision=1)])
 def test_create_rejects_invalid_params(lib, bad):
     from paper_2011_04240_b300 import amto
     plan = ctypes.c_void_p()
@@ -109,3 +113,40 @@ def test_server_null_arguments_rejected(lib):
     assert lib.amto_server_poll(None, 1, 0, None, None) == amto.EINVAL
     assert lib.amto_server_stats(None, None) == amto.EINVAL
     lib.amto_server_destroy(None)  # no-op
+
+
+def test_mixed_null_arguments_rejected(lib):
+    from paper_2011_04240_b300 import amto
+    h = ctypes.c_void_p()
+    assert lib.amto_mixed_create(None, 1, ctypes.byref(h)) == amto.EINVAL
+    plans = (ctypes.c_void_p * 1)(None)
+    assert lib.amto_mixed_create(plans, 1, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 0, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 9, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_solve(None, None, None, None, 1, 0.0, None, None, None,
+                                None) == amto.EINVAL
+    assert lib.amto_mixed_set_trace(None, 1) == amto.EINVAL
+    lib.amto_mixed_destroy(None)  # no-op
+
+
+def test_library_has_no_unresolved_internal_symbols():
+    """Every internal function the library calls is defined in it (a symbol
+    left undefined would only fail when first called on the GPU)."""
+    import subprocess
+    from paper_2011_04240_b300 import amto
+    out = subprocess.run(["nm", "-C", "-u", amto.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    bad = [ln for ln in out.splitlines() if "amto" in ln]
+    assert not bad, bad
+
+
+def test_tune_rejects_invalid_arguments(lib):
+    from paper_2011_04240_b300 import amto
+    r = amto.TuneResult()
+    assert lib.amto_tune(None, 1, 1, ctypes.byref(r)) == amto.EINVAL
+    p = _params(max_batch=4)
+    assert lib.amto_tune(ctypes.byref(p), 5, 10, ctypes.byref(r)) == amto.EINVAL
+    assert lib.amto_tune(ctypes.byref(p), 0, 10, ctypes.byref(r)) == amto.EINVAL
+    assert lib.amto_tune(ctypes.byref(p), 2, 0, ctypes.byref(r)) == amto.EINVAL
+    bad = _params(n_agents=1)
+    assert lib.amto_tune(ctypes.byref(bad), 1, 1, ctypes.byref(r)) == amto.EINVAL
