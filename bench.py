@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--mixed", action="store_true",
                     help="uneven batch only: 512 instances with agent counts uniform in "
                          "{8,16,24,32}, one loop over all counts (fused pair launch)")
+    ap.add_argument("--mixed-group", type=int, default=0,
+                    help="lane group of every agent count in --mixed (0: each plan's own)")
     ap.add_argument("--precision-report", action="store_true",
                     help="errors of every apply precision against the FP64 oracle on 4 "
                          "sampled instances of the batch, at k = 1, 2, 5, 10, 20, 200")
@@ -294,7 +296,7 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
             "iterations": its, "final_resid_max": max(res)}
 
 
-def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32"):
+def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_group=0):
     """Uneven batch: `n_instances` random 8x8x4 m boxes with agent counts drawn
     uniformly from `sizes` (degree 10, m = 100, T = 8 s, literal projection),
     K fixed iterations.  Timed three ways on device-resident inputs: one mixed
@@ -308,7 +310,7 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32"):
     by_n = {n: [p for p in probs if p.n == n] for n in sizes}
     groups = [by_n[n] for n in sizes if by_n[n]]
     pls = [Planner(gr[0].n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, precision=PRECISIONS[prec],
-                   max_batch=len(gr)) for gr in groups]
+                   max_batch=len(gr), tile_group=tile_group) for gr in groups]
     starts, goals = [], []
     for gr in groups:
         s_np, g_np = W.stack(gr)
@@ -501,7 +503,7 @@ def main():
         torch.cuda.set_device(local)
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(mixed_batch(args)), flush=True)
+        print(json.dumps(mixed_batch(args, tile_group=args.mixed_group)), flush=True)
         return
 
     if args.precision_report:

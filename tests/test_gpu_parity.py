@@ -91,11 +91,14 @@ def test_box16_tolerance_stop():
         assert rel_inf(xi[0].reshape(3, -1), st.xi) < XI_TOL
 
 
-@pytest.mark.parametrize("n,m,mode", [(5, 30, "R2"), (16, 100, "R2"), (24, 40, "R3"),
-                                      (33, 17, "R2"), (2, 12, "R2")])
-def test_one_iteration_from_warm_state(n, m, mode):
+@pytest.mark.parametrize("n,m,mode,G,QW", [(5, 30, "R2", 0, 0), (16, 100, "R2", 16, 0),
+                                           (24, 40, "R3", 32, 2), (33, 17, "R2", 0, 0),
+                                           (2, 12, "R2", 0, 3), (32, 60, "R2", 0, 0),
+                                           (16, 100, "R3", 8, 4)])
+def test_one_iteration_from_warm_state(n, m, mode, G, QW):
     """Sub-step parity: from the oracle's own state after 15 iterations, one
-    GPU iteration (projection, QP, alpha/beta, d, lambda) matches the oracle."""
+    GPU iteration (projection, QP, alpha/beta, d, lambda) matches the oracle
+    (every lane group, several time blocks per warp, padded groups)."""
     prob = W.random_box(n, 40 + n, box=(6.0, 6.0, 3.0), m=m, T=6.0)
     M = oracle_mats(prob)
     st15 = oracle_solve(M, prob, 15, mode=mode)
@@ -104,7 +107,7 @@ def test_one_iteration_from_warm_state(n, m, mode):
     p = n * (n - 1) // 2
     ws = O.warm_state(M, xi0.astype(np.float64), lam0.astype(np.float64), mode)
     ref = O.am_iteration(M, ws, O.boundary_values(prob.start, prob.goal), mode)
-    pl = planner(prob, mode)
+    pl = planner(prob, mode, tile_group=G, tile_time_blocks=QW)
     xi, r, k = gpu_solve(pl, [prob], 1, xi_init=xi0.reshape(1, 3, n, -1),
                          lambda_init=lam0.reshape(1, 3, p, m))
     assert k[0] == 1
