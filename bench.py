@@ -316,11 +316,22 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
         s_np, g_np = W.stack(gr)
         starts.append(torch.from_numpy(s_np).cuda())
         goals.append(torch.from_numpy(g_np).cuda())
-    mx = Mixed(pls)
     K, Wm = args.steps, max(args.warmup, 3)
+    stream = torch.cuda.current_stream()
+    # the branch layout (per-count chains overlapping in one graph)
+    mxb = Mixed(pls, amto.MIXED_BRANCHES)
+    outs = mxb.solve(starts, goals, Wm)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(stream)
+    mxb.solve(starts, goals, K, out=outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_branches = e0.elapsed_time(e1)
+    mxb.close()
+    mx = Mixed(pls, amto.MIXED_FUSED)
     outs = mx.solve(starts, goals, Wm)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -367,7 +378,11 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
                        f"{list(sizes)} ({[len(g) for g in groups]} per count), degree 10, "
                        "m=100, T=8 s, literal projection, fixed iterations",
            "apply_precision": prec, "steps": K,
-           "mixed": {"value": n_instances * K / (ms_mixed / 1e3), "ms_per_step": ms_mixed / K},
+           "mixed": {"value": n_instances * K / (ms_mixed / 1e3), "ms_per_step": ms_mixed / K,
+                     "layout": "fused pair launch over all counts"},
+           "mixed_branches": {"value": n_instances * K / (ms_branches / 1e3),
+                              "ms_per_step": ms_branches / K,
+                              "layout": "per-count chains as parallel graph branches"},
            "per_count_sequential": {"value": n_instances * K / (ms_seq / 1e3),
                                     "ms_per_step": ms_seq / K},
            "per_count_concurrent_streams": {"value": n_instances * K / (ms_conc / 1e3),

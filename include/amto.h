@@ -297,9 +297,17 @@ amto_status amto_tune(const amto_params* params, int batch, int iters, amto_tune
  * CUDA graph under a conditional WHILE node (built once per combination of
  * batch sizes), stopping when no instance of any plan is still iterating.
  * Per instance the result is that of amto_solve on its own plan (same
- * arithmetic; only the launches are shared).
+ * arithmetic; only the launches are shared).  The layout (below) chooses
+ * between one fused launch over all plans and per-plan parallel branches.
  * ------------------------------------------------------------------------ */
 #define AMTO_MAX_MIXED_GROUPS 8
+
+/* Layout of a mixed iteration.  FUSED: one right-hand-side launch, one
+ * grouped apply and one persistent pair-step launch over the units of all
+ * plans.  BRANCHES: every plan's own chain (right-hand side, apply, pair
+ * step) as a parallel branch of the graph body, joined by one kernel that
+ * sets the loop condition, so different agent counts overlap on the device. */
+enum { AMTO_MIXED_FUSED = 0, AMTO_MIXED_BRANCHES = 1 };
 
 typedef struct amto_mixed_s* amto_mixed;
 
@@ -308,7 +316,7 @@ typedef struct amto_mixed_s* amto_mixed;
  * plans must outlive the mixed object, and a plan must not be solved by
  * another call while a mixed solve that uses it is in flight.
  * Errors: EINVAL, ENOMEM, ECUDA. */
-amto_status amto_mixed_create(const amto_plan* plans, int n_plans, amto_mixed* out);
+amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, amto_mixed* out);
 
 /* Solve batch[g] instances with plan g, for every g, as one loop; arguments
  * per group are as in amto_solve (all six boundary conditions from start and

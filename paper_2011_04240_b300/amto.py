@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
 APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED = range(3)
+MIXED_FUSED, MIXED_BRANCHES = range(2)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
 STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",
@@ -105,7 +106,8 @@ SIGNATURES = {
     "amto_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
     "amto_tune": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(TuneResult)]),
-    "amto_mixed_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "amto_mixed_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(_P)]),
     "amto_mixed_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
                                         ctypes.POINTER(_P), ctypes.c_int, ctypes.c_float,
                                         ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -344,13 +346,13 @@ class Mixed:
     ([B_g, n_g, 3] each) and returns one (xi, resid, iters) per planner.
     """
 
-    def __init__(self, planners):
+    def __init__(self, planners, layout: int = 0):
         import torch
         self._torch = torch
         self.planners = list(planners)
         arr = (_P * len(self.planners))(*[p.plan for p in self.planners])
         h = _P()
-        _check(load().amto_mixed_create(arr, len(self.planners), ctypes.byref(h)))
+        _check(load().amto_mixed_create(arr, len(self.planners), int(layout), ctypes.byref(h)))
         self.handle = h.value
 
     def solve(self, starts, goals, max_iters: int, tol: float = 0.0, out=None, stream=None):

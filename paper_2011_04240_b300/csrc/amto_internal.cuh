@@ -164,6 +164,8 @@ amto_status tc_configure(amto_plan_s* pl);
 // Mixed batches (several plans iterated as one loop; csrc/mixed.cu).
 amto_status launch_ctl_reset(Ctl* ctl, int max_iters, float tol, cudaStream_t s);
 amto_status launch_rhs_mixed(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
+amto_status launch_mixed_cond(amto_plan_s* const* pls, int ng, Ctl* ctl,
+                              cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 amto_status launch_apply_mixed(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
 amto_status configure_pair_mixed(amto_plan_s* const* pls, int ng, int* grid);
 amto_status launch_pair_mixed(amto_plan_s* const* pls, const int* batch, int ng, Ctl* ctl,

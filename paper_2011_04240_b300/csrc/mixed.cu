@@ -14,7 +14,12 @@
 // conditional WHILE node; the last block of k_pair_mixed sets the condition
 // from the flags of all plans.  Small and large instances therefore share
 // the SMs within each launch instead of running as separate, partly empty
-// launches per agent count.
+// launches per agent count (layout AMTO_MIXED_FUSED).  Layout
+// AMTO_MIXED_BRANCHES instead runs every plan's own chain (right-hand side,
+// apply, pair step) as a parallel branch of the graph body, joined by one
+// kernel that sets the loop condition: the chains of different agent counts
+// overlap on the device, so one count's apply runs beside another's pair
+// step.
 #include <map>
 #include <new>
 #include <string>
@@ -24,6 +29,9 @@
 
 struct amto_mixed_s {
     std::vector<amto_plan_s*> pls;
+    int layout = AMTO_MIXED_FUSED;
+    std::vector<cudaStream_t> br;      // BRANCHES: one stream per plan
+    std::vector<cudaEvent_t> ev;       // BRANCHES: fork event, then one join event per plan
     int device = 0;
     int grid = 0;                  // persistent grid of the fused pair kernel
     amto::Ctl* ctl = nullptr;      // loop control (device)
@@ -39,6 +47,22 @@ namespace {
 amto_status mixed_body(amto_mixed_s* mx, const std::vector<int>& batch,
                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
     const int ng = (int)mx->pls.size();
+    if (mx->layout == AMTO_MIXED_BRANCHES) {
+        // each plan's chain on its own stream (parallel branches of the graph
+        // body), joined by one kernel that sets the loop condition
+        AMTO_CUDA_TRY(cudaEventRecord(mx->ev[0], s));
+        for (int g = 0; g < ng; ++g) {
+            cudaStream_t b = mx->br[g];
+            AMTO_CUDA_TRY(cudaStreamWaitEvent(b, mx->ev[0], 0));
+            amto_status st = launch_rhs(mx->pls[g], batch[g], b);
+            if (st == AMTO_OK) st = launch_apply(mx->pls[g], batch[g], b);
+            if (st == AMTO_OK) st = launch_pair(mx->pls[g], batch[g], 0, nullptr, 0, 0, b);
+            if (st != AMTO_OK) return st;
+            AMTO_CUDA_TRY(cudaEventRecord(mx->ev[1 + g], b));
+            AMTO_CUDA_TRY(cudaStreamWaitEvent(s, mx->ev[1 + g], 0));
+        }
+        return launch_mixed_cond(mx->pls.data(), ng, mx->ctl, h, use_cond, s);
+    }
     amto_status st = launch_rhs_mixed(mx->pls.data(), batch.data(), ng, s);
     if (st == AMTO_OK) st = launch_apply_mixed(mx->pls.data(), batch.data(), ng, s);
     if (st == AMTO_OK)
@@ -98,6 +122,8 @@ void free_mixed(amto_mixed_s* mx) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
+    for (cudaStream_t b : mx->br) cudaStreamDestroy(b);
+    for (cudaEvent_t e : mx->ev) cudaEventDestroy(e);
     if (mx->ctl) cudaFree(mx->ctl);
     if (mx->ctl_host) cudaFreeHost(mx->ctl_host);
     if (mx->cap) cudaStreamDestroy(mx->cap);
@@ -111,13 +137,17 @@ using namespace amto;
 
 extern "C" {
 
-amto_status amto_mixed_create(const amto_plan* plans, int n_plans, amto_mixed* out) {
+amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, amto_mixed* out) {
     clear_error();
     if (!out || !plans) {
         set_error("invalid argument: plans and out are required");
         return AMTO_EINVAL;
     }
     *out = nullptr;
+    if (layout != AMTO_MIXED_FUSED && layout != AMTO_MIXED_BRANCHES) {
+        set_error("invalid argument: layout must be AMTO_MIXED_FUSED or AMTO_MIXED_BRANCHES");
+        return AMTO_EINVAL;
+    }
     if (n_plans < 1 || n_plans > AMTO_MAX_MIXED_GROUPS) {
         set_error("invalid argument: n_plans must be in [1, AMTO_MAX_MIXED_GROUPS]");
         return AMTO_EINVAL;
@@ -148,6 +178,7 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, amto_mixed* o
         return AMTO_ENOMEM;
     }
     mx->pls.assign(plans, plans + n_plans);
+    mx->layout = layout;
     mx->device = plans[0]->device;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -165,6 +196,25 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, amto_mixed* o
         st = AMTO_ECUDA;
     }
     if (st == AMTO_OK) st = configure_pair_mixed(mx->pls.data(), n_plans, &mx->grid);
+    for (int g = 0; g <= n_plans && st == AMTO_OK && layout == AMTO_MIXED_BRANCHES; ++g) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaEventCreate failed");
+            st = AMTO_ECUDA;
+            break;
+        }
+        mx->ev.push_back(e);
+        if (g == n_plans) break;
+        cudaStream_t b = nullptr;
+        if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaStreamCreate failed");
+            st = AMTO_ECUDA;
+            break;
+        }
+        mx->br.push_back(b);
+    }
     if (prev >= 0 && prev != mx->device) cudaSetDevice(prev);
     if (st != AMTO_OK) {
         free_mixed(mx);

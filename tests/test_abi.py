@@ -118,11 +118,12 @@ def test_server_null_arguments_rejected(lib):
 def test_mixed_null_arguments_rejected(lib):
     from paper_2011_04240_b300 import amto
     h = ctypes.c_void_p()
-    assert lib.amto_mixed_create(None, 1, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(None, 1, 0, ctypes.byref(h)) == amto.EINVAL
     plans = (ctypes.c_void_p * 1)(None)
-    assert lib.amto_mixed_create(plans, 1, ctypes.byref(h)) == amto.EINVAL
-    assert lib.amto_mixed_create(plans, 0, ctypes.byref(h)) == amto.EINVAL
-    assert lib.amto_mixed_create(plans, 9, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 1, 0, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 0, 0, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 9, 0, ctypes.byref(h)) == amto.EINVAL
+    assert lib.amto_mixed_create(plans, 1, 2, ctypes.byref(h)) == amto.EINVAL
     assert lib.amto_mixed_solve(None, None, None, None, 1, 0.0, None, None, None,
                                 None) == amto.EINVAL
     assert lib.amto_mixed_set_trace(None, 1) == amto.EINVAL

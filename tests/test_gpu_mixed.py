@@ -47,16 +47,20 @@ def _plan(prob, B, precision="fp32", apply_mode=0):
                    precision=PRECISIONS[precision], apply_mode=apply_mode)
 
 
-@pytest.mark.parametrize("precision,apply_mode", [("fp32", 0), ("fp32", 1), ("tf32x3", 0)])
-def test_mixed_matches_per_plan_solves_and_oracle(precision, apply_mode):
-    """apply_mode 0 with float32: every group applies K^-1 inside the fused
-    pair kernel (one launch per iteration); 1: grouped right-hand-side and
-    GEMM launches; tf32x3: per-group tensor-core GEMMs."""
+@pytest.mark.parametrize("precision,apply_mode,layout", [("fp32", 2, 0), ("fp32", 1, 0),
+                                                          ("tf32x3", 0, 0), ("fp32", 0, 1),
+                                                          ("tf32x3", 0, 1), ("fp32", 2, 1)])
+def test_mixed_matches_per_plan_solves_and_oracle(precision, apply_mode, layout):
+    """apply_mode 2: every group applies K^-1 inside the pair kernel (one
+    launch per iteration); 1 (and 0 = automatic): grouped right-hand-side and
+    GEMM launches (per-group tensor-core GEMMs for tf32x3).  layout 0: one
+    fused pair launch over all groups; 1: per-group chains as parallel
+    branches of the graph."""
     from paper_2011_04240_b300 import Mixed
     sizes, batches = (8, 16, 24, 32, 5), (6, 5, 7, 5, 6)
     groups = _groups(sizes, batches, 11)
     pls = [_plan(gr[0], 8, precision, apply_mode) for gr in groups]
-    mx = Mixed(pls)
+    mx = Mixed(pls, layout)
     res = _mixed_solve(mx, groups, 10)
     for g, probs in enumerate(groups):
         x, r, k = res[g]
@@ -68,12 +72,13 @@ def test_mixed_matches_per_plan_solves_and_oracle(precision, apply_mode):
     mx.close()
 
 
-def test_mixed_tolerance_stop_per_instance_and_trace_mode():
+@pytest.mark.parametrize("layout", [0, 1])
+def test_mixed_tolerance_stop_per_instance_and_trace_mode(layout):
     from paper_2011_04240_b300 import Mixed
     sizes, batches = (8, 16, 24, 32), (16, 16, 16, 16)
     groups = _groups(sizes, batches, 23)
     pls = [planner(gr[0], max_batch=16) for gr in groups]
-    mx = Mixed(pls)
+    mx = Mixed(pls, layout)
     res = _mixed_solve(mx, groups, 500, tol=1e-2)
     mx.set_trace(True)
     res_t = _mixed_solve(mx, groups, 500, tol=1e-2)

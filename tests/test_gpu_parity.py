@@ -199,3 +199,26 @@ def test_plans_created_in_any_order_keep_their_launch_limits():
     assert np.all(np.isfinite(r48)) and np.all(np.isfinite(r64))
     st = oracle_solve(oracle_mats(p48), p48, 2)
     assert rel_inf(x48[0].reshape(3, -1), st.xi) < 1e-4
+
+
+@pytest.mark.parametrize("n,mode,k,B", [(16, "R2", 30, 4), (64, "R3", 3, 2), (24, "R2", 200, 3)])
+def test_fp64_final_residual_is_the_maximum(n, mode, k, B):
+    """The reported residual (float32 screen, FP64 recomputation of the
+    candidates) is the maximum over all pairs and samples: with lambda^(k-1)
+    and lambda^k read back (solves are deterministic), max ||f_c|| =
+    max ||lambda^k - lambda^(k-1)|| / rho up to float32 rounding of lambda."""
+    if n == 64:
+        probs = W.config4(B)
+    else:
+        probs = [W.random_box(n, 900 + i, box=(8.0, 8.0, 4.0)) for i in range(B)]
+    pl = planner(probs[0], mode, max_batch=B)
+    gpu_solve(pl, probs, k - 1)
+    lam_a = gpu_state(pl)[0].astype(np.float64)
+    x, r, kk = gpu_solve(pl, probs, k)
+    lam_b = gpu_state(pl)[0].astype(np.float64)
+    assert np.all(kk == k)
+    for i in range(B):
+        fc = np.sqrt(((lam_b[i] - lam_a[i]) ** 2).sum(axis=0)) / probs[i].rho
+        ref = fc.max()
+        tol = 1e-6 * max(np.abs(lam_b[i]).max(), 1.0) + 1e-6 * ref
+        assert abs(r[i] - ref) <= tol, (i, r[i], ref)
