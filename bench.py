@@ -145,10 +145,19 @@ def algorithmic_pair_bytes(n, m, batch):
 
 
 def source_hash():
+    """Hash of the pair kernel's source: iterate.cu up to the right-hand-side
+    section (geometry, setup, pair kernels) plus its launcher and the
+    library's shared header; other kernels can change without invalidating
+    the recorded pair-kernel traffic."""
+    src = open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", "iterate.cu")).read()
+    head = src.split("// Right-hand side of the increment form")[0]
+    m = re.search(r"\nPairArgs pair_args\(.*?\n}\n.*?\namto_status launch_pair\(.*?\n}\n", src,
+                  re.S)
     h = hashlib.sha256()
-    for f in ["iterate.cu"]:
-        with open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(head.encode())
+    h.update(m.group(0).encode() if m else b"")
+    h.update(open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", "amto_internal.cuh"),
+                  "rb").read())
     return h.hexdigest()[:16]
 
 
