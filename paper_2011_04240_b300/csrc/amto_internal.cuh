@@ -64,9 +64,9 @@ struct PairGeom {
     int grid;       // persistent pair-kernel blocks (set when the kernels are configured)
 };
 
-// Pair-kernel geometry for n agents and m samples: lane group G (0: the one
-// with the least padding) and time blocks per warp and unit QW (0: automatic).
-PairGeom choose_geometry(int n, int m, int G_req = 0, int QW_req = 0);
+// Pair-kernel geometry for n agents and m samples: lane group G and time
+// blocks per warp and unit QW (0: automatic, depending on the batch size).
+PairGeom choose_geometry(int n, int m, int G_req, int QW_req, int max_batch);
 
 struct Graph {
     cudaGraph_t graph = nullptr;

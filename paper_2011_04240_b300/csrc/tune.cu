@@ -119,7 +119,7 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
             p.tile_time_blocks = qws[qi];
             p.apply_mode = modes[mi];
             p.max_batch = batch;
-            const PairGeom g = choose_geometry(n, p.m_steps, G, qws[qi]);
+            const PairGeom g = choose_geometry(n, p.m_steps, G, qws[qi], batch);
             if (qws[qi] > 1 && g.TC / 2 >= p.m_steps) continue;  // one unit covers the horizon
             if (validate_params(p) != AMTO_OK) {
                 clear_error();
