@@ -131,6 +131,22 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
     return out
 
 
+def max_over_ranks(x, world, device):
+    """Largest x over all ranks: the job ends when its slowest rank does."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job rate: every rank processes its own units (replicas, weak
+    scaling); the elapsed time is the slowest rank's."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def workload(args, rank):
     import workloads as W
     probs = W.config4(args.batch, seed=rank, n=args.agents)
@@ -472,6 +488,35 @@ def precision_report(args, ks=(1, 2, 5, 10, 20, 200), samples=(0, 85, 170, 255))
     return out
 
 
+def config1_latency(reps=5):
+    """4 agents on a 3 m circle, antipodal goals, m = 50, T = 5 s, 200 fixed
+    iterations, literal projection, batch 1: wall time of one solve on the
+    device (setup, 200 iterations, FP64 residual) and per iteration."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Planner
+    p = W.config1()
+    pl = Planner(4, 50, 5.0, max_batch=1)
+    s = torch.from_numpy(p.start[None]).cuda()
+    g = torch.from_numpy(p.goal[None]).cuda()
+    pl.solve(s, g, 200)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        xi, r, k = pl.solve(s, g, 200)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    pl.close()
+    ms = float(np.median(ts))
+    return {"workload": "4 agents, 3 m circle, antipodal, m=50, T=5 s, 200 iterations, batch 1",
+            "ms_per_solve": ms, "us_per_iteration": 1e3 * ms / 200,
+            "value": 200 / (ms / 1e3), "unit": UNIT, "final_resid": float(r.item())}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
     if rank != 0:
@@ -592,11 +637,8 @@ def main():
     ms = e0.elapsed_time(e1)
     iters_done = int(out[2].sum().item())
     assert iters_done == B * K, (iters_done, B * K)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * B * K / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = job_throughput(B * K, world, ms_max)
 
     extras = {}
     if not args.no_extras:
@@ -618,13 +660,10 @@ def main():
         hk.copy_(out[2], non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = f0.elapsed_time(f1)
-        e2e_t = torch.tensor([e2e_ms], device="cuda")
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_max = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
         h2d = (hs.numel() + hg.numel()) * 4
         d2h = hx.numel() * 4 + hr.numel() * 4 + hk.numel() * 4
-        extras["e2e"] = {"value": world * B * K / (float(e2e_t.item()) / 1e3), "unit": UNIT,
+        extras["e2e"] = {"value": job_throughput(B * K, world, e2e_max), "unit": UNIT,
                          "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                          "note": "one solve of K iterations per timed call; bytes per solve / K"}
         # per-kernel device time from an event-traced pass of the same solve
@@ -648,6 +687,7 @@ def main():
                                                           "apply": kms[2] / max(kcnt[2], 1)}}
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
+            extras["config1_latency"] = config1_latency()
             extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:
