@@ -172,8 +172,8 @@ def source_hash():
     h = hashlib.sha256()
     h.update(head.encode())
     h.update(m.group(0).encode() if m else b"")
-    h.update(open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", "amto_internal.cuh"),
-                  "rb").read())
+    for f in ("amto_internal.cuh", "schedule.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

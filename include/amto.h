@@ -96,7 +96,19 @@ typedef struct {
     int tile_group;
     int tile_time_blocks;
     int apply_mode;    /* AMTO_APPLY_*: where the cached inverse is applied */
+    int loop_mode;     /* AMTO_LOOP_*: how the iterations are driven */
 } amto_params;
+
+/* How the loop of Algorithm 1 runs.  GRAPH: one CUDA graph per batch size,
+ * a conditional WHILE node around the iteration's kernels (right-hand side,
+ * apply, pair step), every instance of the batch in every launch.  BLOCK
+ * (float32, batched apply): one thread block per instance runs the whole
+ * loop (right-hand side, K^-1 matrix-vector product from L2, pair step, the
+ * stopping rule) with no launch between iterations; for small instances and
+ * latency-bound solves.  AUTO: BLOCK for float32 plans with n_agents <= 8
+ * and max_batch <= 148 (one wave of blocks), else GRAPH (measured crossover
+ * on B300; amto_tune measures both). */
+enum { AMTO_LOOP_AUTO = 0, AMTO_LOOP_GRAPH = 1, AMTO_LOOP_BLOCK = 2 };
 
 /* Where the step xi += K^-1_top [g; e] runs.  BATCHED: a separate right-hand-
  * side launch and one GEMM launch over the batch per iteration (tensor cores
@@ -123,6 +135,7 @@ typedef struct {
                                            initial projection, FP64 residual, outputs */
     int time_blocks;                    /* pair-kernel time blocks per warp and unit */
     int apply_mode;                     /* AMTO_APPLY_BATCHED or AMTO_APPLY_FUSED */
+    int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
 } amto_info;
 
 /*
@@ -257,12 +270,13 @@ amto_status amto_set_trace(amto_plan plan, int on);
  * changes which lanes and blocks process which pairs and samples, never a
  * result.
  * ------------------------------------------------------------------------ */
-#define AMTO_TUNE_MAX 32
+#define AMTO_TUNE_MAX 48
 
 typedef struct {
     int tile_group;            /* agents per lane group: 8, 16 or 32 */
     int tile_time_blocks;      /* time blocks per warp and work unit */
     int apply_mode;            /* AMTO_APPLY_BATCHED or AMTO_APPLY_FUSED */
+    int loop_mode;             /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
     double us_per_iteration;   /* measured loop time per iteration of the batch */
 } amto_tune_entry;
 
@@ -272,13 +286,13 @@ typedef struct {
     int best;                                /* index of the fastest entry */
 } amto_tune_result;
 
-/* Measure every tile (and, for float32 plans, both apply modes) that fits
- * `params` (its tile and apply_mode fields are ignored) on a
+/* Measure every tile (and, for float32 plans, the apply and loop modes) that
+ * fits `params` (its tile, apply_mode and loop_mode fields are ignored) on a
  * synthetic batch of `batch` instances (agents on a ring, antipodal goals),
  * `iters` fixed iterations each: a plan per candidate is created, solved
  * twice (2 and 2 + iters iterations, the difference is the loop time) and
  * destroyed.  Synchronous; uses the current device.  Copy the best entry's
- * three fields into amto_params before amto_create.
+ * four fields into amto_params before amto_create.
  * Errors: EINVAL (bad params, 1 <= batch <= max_batch, 1 <= iters <= 1e5),
  * ENOMEM, ECUDA. */
 amto_status amto_tune(const amto_params* params, int batch, int iters, amto_tune_result* out);

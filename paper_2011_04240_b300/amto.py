@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
 APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED = range(3)
+LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
 MIXED_FUSED, MIXED_BRANCHES = range(2)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
@@ -41,7 +42,7 @@ class Params(ctypes.Structure):
                 ("bc_mask", ctypes.c_uint), ("proj_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
-                ("apply_mode", ctypes.c_int)]
+                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -51,7 +52,7 @@ class Info(ctypes.Structure):
                 ("lambda_floats", ctypes.c_longlong), ("kkt_check", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
                 ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
-                ("apply_mode", ctypes.c_int)]
+                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -83,11 +84,12 @@ class ServerStats(ctypes.Structure):
 
 class TuneEntry(ctypes.Structure):
     _fields_ = [("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
-                ("apply_mode", ctypes.c_int), ("us_per_iteration", ctypes.c_double)]
+                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
+                ("us_per_iteration", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("n_entries", ctypes.c_int), ("entries", TuneEntry * 32), ("best", ctypes.c_int)]
+    _fields_ = [("n_entries", ctypes.c_int), ("entries", TuneEntry * 48), ("best", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -213,14 +215,15 @@ def set_trace(plan, on: bool) -> None:
 
 
 def tune(params: Params, batch: int, iters: int = 20) -> dict:
-    """Measure the pair-kernel tiles (and apply modes) for `params` on a
-    synthetic batch; returns {"best": (tile_group, tile_time_blocks,
-    apply_mode), "entries": [(G, QW, apply_mode, us/iteration)]}."""
+    """Measure the pair-kernel tiles (and apply and loop modes) for `params`
+    on a synthetic batch; returns {"best": (tile_group, tile_time_blocks,
+    apply_mode, loop_mode), "entries": [(G, QW, apply_mode, loop_mode,
+    us/iteration)]}."""
     r = TuneResult()
     _check(load().amto_tune(ctypes.byref(params), int(batch), int(iters), ctypes.byref(r)))
     ent = [(r.entries[i].tile_group, r.entries[i].tile_time_blocks, r.entries[i].apply_mode,
-            r.entries[i].us_per_iteration) for i in range(r.n_entries)]
-    return {"best": ent[r.best][:3], "entries": ent}
+            r.entries[i].loop_mode, r.entries[i].us_per_iteration) for i in range(r.n_entries)]
+    return {"best": ent[r.best][:4], "entries": ent}
 
 
 def last_error() -> str:
@@ -246,13 +249,13 @@ class Planner:
                  rho: float = 1.0, poly_degree: int = 10, bc_mask: int = BC_ALL,
                  proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
-                 apply_mode: int = 0):
+                 apply_mode: int = 0, loop_mode: int = 0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
-                             apply_mode)
+                             apply_mode, loop_mode)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)

@@ -123,6 +123,7 @@ struct amto_plan_s {
 
     int last_batch = 0;
     bool fused = false;        // K^-1 applied per instance inside the pair kernel
+    bool block = false;        // the loop runs in the one-block-per-instance solver
     cudaStream_t cap_stream = nullptr;
     std::map<int, amto::Graph> graphs;
 
@@ -171,6 +172,15 @@ amto_status configure_pair_mixed(amto_plan_s* const* pls, int ng, int* grid);
 amto_status launch_pair_mixed(amto_plan_s* const* pls, const int* batch, int ng, Ctl* ctl,
                               int grid, cudaGraphConditionalHandle h, int use_cond,
                               cudaStream_t s);
+// One-block-per-instance solver (csrc/block_solve.cu): the whole loop of
+// every listed plan's batch in one launch (after setup and the initial
+// projection, before the final residual).
+size_t block_solver_smem(const PairGeom& g, int n, int m, int nv, int nb);
+amto_status configure_block_solver(amto_plan_s* pl);
+// Whether a plan with these parameters runs its loop in the block solver.
+bool loop_block(const amto_params& p);
+amto_status launch_block_solver(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
+cudaError_t raise_smem_cap(const void* fn, size_t bytes);
 // Tile grid, split-K count and K per split of the tensor-core apply.
 void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, int* kper);
 // Kernel launches of one iteration of a batch-`batch` solve.

@@ -178,6 +178,11 @@ amto_status validate_params(const amto_params& p) {
         return einval("apply_mode must be one of AMTO_APPLY_*");
     if (p.apply_mode == AMTO_APPLY_FUSED && p.precision != AMTO_PREC_FP32)
         return einval("the fused apply is float32 (AMTO_PREC_FP32) only");
+    if (p.loop_mode < AMTO_LOOP_AUTO || p.loop_mode > AMTO_LOOP_BLOCK)
+        return einval("loop_mode must be one of AMTO_LOOP_*");
+    if (p.loop_mode == AMTO_LOOP_BLOCK &&
+        (p.precision != AMTO_PREC_FP32 || p.apply_mode == AMTO_APPLY_FUSED))
+        return einval("the block solver is float32 with the batched apply only");
     if (p.tile_group != 0 && p.tile_group != 8 && p.tile_group != 16 && p.tile_group != 32)
         return einval("tile_group must be 0 (automatic), 8, 16 or 32");
     if (p.tile_time_blocks < 0 || p.tile_time_blocks > 8)
@@ -189,6 +194,10 @@ amto_status validate_params(const amto_params& p) {
                                  g.TC, g.npad, apply_fused(p)) > 227 * 1024)
             return einval("the pair-kernel tile does not fit in shared memory; use fewer "
                           "time blocks per warp");
+        if (p.loop_mode == AMTO_LOOP_BLOCK &&
+            block_solver_smem(g, p.n_agents, p.m_steps, p.poly_degree + 1,
+                              __builtin_popcount(p.bc_mask)) > 227 * 1024)
+            return einval("this instance is too large for the block solver; use AMTO_LOOP_GRAPH");
     }
     return AMTO_OK;
 }
@@ -233,6 +242,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch);
     pl->fused = apply_fused(p);
+    pl->block = loop_block(p);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
     pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
     const bool tc = prec_tc(p.precision), bf = prec_bf16(p.precision);
@@ -297,6 +307,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     if (st == AMTO_OK) st = precompute(pl);
     if (st == AMTO_OK && tc) st = tc_configure(pl);
+    if (st == AMTO_OK && pl->block) st = configure_block_solver(pl);
     if (st == AMTO_OK && cudaMemset(pl->flags, 0, sizeof(int) * B) != cudaSuccess) {
         set_error("cudaMemset failed");
         st = AMTO_ECUDA;
@@ -342,7 +353,10 @@ amto_status amto_solve(amto_plan plan, int batch, const float* start, const floa
     if (st != AMTO_OK) return st;
     st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, 0, 0, s);
     if (st != AMTO_OK) return st;
-    if (plan->trace) {
+    if (plan->block) {
+        amto_plan_s* one[1] = {plan};
+        st = launch_block_solver(one, &batch, 1, s);
+    } else if (plan->trace) {
         for (int k = 0; k < KSTAT_N; ++k) {
             plan->stat_ms[k] = 0.0;
             plan->stat_cnt[k] = 0;
@@ -392,6 +406,11 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->launches_fixed = 4;
     out->time_blocks = plan->geo.QW;
     out->apply_mode = plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
+    out->loop_mode = plan->block ? AMTO_LOOP_BLOCK : AMTO_LOOP_GRAPH;
+    if (plan->block) {
+        out->launches_per_iteration = 0;
+        out->launches_fixed = 5;  // setup, initial projection, block solver, residual, outputs
+    }
     return AMTO_OK;
 }
 

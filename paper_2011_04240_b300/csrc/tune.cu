@@ -7,7 +7,8 @@
 // work unit (larger units amortise the unit prologue and epilogue; smaller
 // ones balance the persistent grid).  For float32 plans the apply mode is a
 // third choice (one batched GEMM launch, or a matrix-vector product fused
-// into the pair kernel).  amto_tune measures every candidate that fits on a
+// into the pair kernel), and so is the loop (the graph loop, or one block per
+// instance running the whole loop).  amto_tune measures every candidate that fits on a
 // synthetic batch of the caller's shape and reports them all.
 #include <chrono>
 #include <cmath>
@@ -68,6 +69,7 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
     base.tile_group = 0;
     base.tile_time_blocks = 0;
     base.apply_mode = AMTO_APPLY_AUTO;
+    base.loop_mode = AMTO_LOOP_AUTO;
     if (validate_params(base) != AMTO_OK) return AMTO_EINVAL;
     if (batch < 1 || batch > base.max_batch || iters < 1 || iters > 100000) {
         set_error("invalid argument: 1 <= batch <= max_batch and 1 <= iters <= 100000");
@@ -107,8 +109,10 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
     };
     const int groups[3] = {8, 16, 32};
     const int qws[4] = {1, 2, 4, 8};
-    const int modes[2] = {AMTO_APPLY_BATCHED, AMTO_APPLY_FUSED};
-    const int n_modes = base.precision == AMTO_PREC_FP32 ? 2 : 1;
+    // (apply mode, loop mode): batched + graph, fused + graph, batched + block
+    const int modes[3] = {AMTO_APPLY_BATCHED, AMTO_APPLY_FUSED, AMTO_APPLY_BATCHED};
+    const int loops[3] = {AMTO_LOOP_GRAPH, AMTO_LOOP_GRAPH, AMTO_LOOP_BLOCK};
+    const int n_modes = base.precision == AMTO_PREC_FP32 ? 3 : 1;
     for (int mi = 0; mi < n_modes && st == AMTO_OK; ++mi)
     for (int gi = 0; gi < 3 && st == AMTO_OK; ++gi) {
         const int G = groups[gi];
@@ -118,7 +122,9 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
             p.tile_group = G;
             p.tile_time_blocks = qws[qi];
             p.apply_mode = modes[mi];
+            p.loop_mode = loops[mi];
             p.max_batch = batch;
+            if (loops[mi] == AMTO_LOOP_BLOCK && qws[qi] > 1) continue;  // no time blocks per warp
             const PairGeom g = choose_geometry(n, p.m_steps, G, qws[qi], batch);
             if (qws[qi] > 1 && g.TC / 2 >= p.m_steps) continue;  // one unit covers the horizon
             if (validate_params(p) != AMTO_OK) {
@@ -139,6 +145,7 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
             e.tile_group = G;
             e.tile_time_blocks = qws[qi];
             e.apply_mode = modes[mi];
+            e.loop_mode = loops[mi];
             e.us_per_iteration = 1e3 * (double)(t_long - t_short) / iters;
             if (out->best < 0 || e.us_per_iteration < out->entries[out->best].us_per_iteration)
                 out->best = out->n_entries;

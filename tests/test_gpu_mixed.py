@@ -41,10 +41,12 @@ def _mixed_solve(mx, groups, iters, tol=0.0):
 
 
 def _plan(prob, B, precision="fp32", apply_mode=0):
+    """Plans in the graph loop: the per-plan reference solves then run the
+    same kernels as the mixed loop."""
     from paper_2011_04240_b300 import Planner
     from tests.gpu_helpers import PRECISIONS
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree, max_batch=B,
-                   precision=PRECISIONS[precision], apply_mode=apply_mode)
+                   precision=PRECISIONS[precision], apply_mode=apply_mode, loop_mode=1)
 
 
 @pytest.mark.parametrize("precision,apply_mode,layout", [("fp32", 2, 0), ("fp32", 1, 0),
@@ -77,7 +79,7 @@ def test_mixed_tolerance_stop_per_instance_and_trace_mode(layout):
     from paper_2011_04240_b300 import Mixed
     sizes, batches = (8, 16, 24, 32), (16, 16, 16, 16)
     groups = _groups(sizes, batches, 23)
-    pls = [planner(gr[0], max_batch=16) for gr in groups]
+    pls = [planner(gr[0], max_batch=16, loop_mode=1) for gr in groups]
     mx = Mixed(pls, layout)
     res = _mixed_solve(mx, groups, 500, tol=1e-2)
     mx.set_trace(True)

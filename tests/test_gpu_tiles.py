@@ -20,11 +20,12 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _planner(prob, B, G=0, QW=0, mode=0, apply_mode=0, precision=0):
+def _planner(prob, B, G=0, QW=0, mode=0, apply_mode=0, precision=0, loop_mode=1):
+    """Graph-loop plans (the tiles and apply modes under test are its)."""
     from paper_2011_04240_b300 import Planner
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree, proj_mode=mode,
                    max_batch=B, tile_group=G, tile_time_blocks=QW, apply_mode=apply_mode,
-                   precision=precision)
+                   precision=precision, loop_mode=loop_mode)
 
 
 @pytest.mark.parametrize("n,m,G,QW", [(16, 100, 8, 1), (16, 100, 8, 4), (16, 100, 16, 2),
@@ -52,14 +53,15 @@ def test_tiling_matches_oracle_and_automatic(n, m, G, QW):
 def test_tune_measures_candidates():
     from paper_2011_04240_b300 import amto
     prob = W.random_box(16, 1, box=(8.0, 8.0, 4.0))
-    p = amto.Params(16, 100, 10, 8.0, 0.6, 1.2, 1.0, 63, 0, 0, 8, 0, 0, 0)
+    p = amto.Params(16, 100, 10, 8.0, 0.6, 1.2, 1.0, 63, 0, 0, 8, 0, 0, 0, 0)
     res = amto.tune(p, 8, 5)
-    assert len(res["entries"]) >= 8
+    assert len(res["entries"]) >= 10
     assert {e[0] for e in res["entries"]} == {8, 16}
     assert {e[2] for e in res["entries"]} == {amto.APPLY_BATCHED, amto.APPLY_FUSED}
-    assert all(e[3] > 0 for e in res["entries"])
-    assert res["best"] in [e[:3] for e in res["entries"]]
-    G, QW, mode = res["best"]
+    assert {e[3] for e in res["entries"]} == {amto.LOOP_GRAPH, amto.LOOP_BLOCK}
+    assert all(e[4] > 0 for e in res["entries"])
+    assert res["best"] in [e[:4] for e in res["entries"]]
+    G, QW, mode, loop = res["best"]
     pl = _planner(prob, 2, G, QW, apply_mode=mode)
     x, r, k = gpu_solve(pl, [prob, prob], 3)
     assert np.all(k == 3)
