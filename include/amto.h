@@ -116,8 +116,19 @@ enum { AMTO_LOOP_AUTO = 0, AMTO_LOOP_GRAPH = 1, AMTO_LOOP_BLOCK = 2 };
  * instance's pair step forms its right-hand side and applies K^-1 as a
  * matrix-vector product (K^-1 read from L2), so an iteration is one launch.
  * AUTO: BATCHED (faster on B300 at every size measured; amto_tune measures
- * both). */
-enum { AMTO_APPLY_AUTO = 0, AMTO_APPLY_BATCHED = 1, AMTO_APPLY_FUSED = 2 };
+ * both).  KRONECKER (any precision; the apply itself is float32): the exact
+ * agent structure of the inverse, K^-1 = I (x) K_n^-1 + (1/n) 1 1^T (x)
+ * (K_0^-1 - K_n^-1) with K_n, K_0 the agent-level KKT matrices with
+ * smoothness plus rho n P^T P and smoothness only, applied as
+ * xi_i += K_n^-1_top (r_i - r_mean) + K_0^-1_top r_mean: O(17^2 n) per axis
+ * instead of the dense O(187 n^2); the same result in exact arithmetic,
+ * not the paper's dense product (a variant, measured against it). */
+enum {
+    AMTO_APPLY_AUTO = 0,
+    AMTO_APPLY_BATCHED = 1,
+    AMTO_APPLY_FUSED = 2,
+    AMTO_APPLY_KRONECKER = 3
+};
 
 typedef struct {
     int n_agents, m_steps, nv, nb;      /* nv = N+1 coefficients, nb = #BC rows */
@@ -134,7 +145,7 @@ typedef struct {
     int launches_fixed;                 /* kernels per solve outside the loop: setup,
                                            initial projection, FP64 residual, outputs */
     int time_blocks;                    /* pair-kernel time blocks per warp and unit */
-    int apply_mode;                     /* AMTO_APPLY_BATCHED or AMTO_APPLY_FUSED */
+    int apply_mode;                     /* AMTO_APPLY_BATCHED, _FUSED or _KRONECKER */
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
 } amto_info;
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libamto.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
-APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED = range(3)
+APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED, APPLY_KRONECKER = range(4)
 LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
 MIXED_FUSED, MIXED_BRANCHES = range(2)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63

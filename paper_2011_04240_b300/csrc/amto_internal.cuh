@@ -91,6 +91,7 @@ struct amto_plan_s {
     float* Q32 = nullptr;      // [nv][nv]  Pddot^T Pddot
     float* A32 = nullptr;      // [nb][nv]
     float* E0 = nullptr;       // [nv][nb]  top-right block of the agent-level inverse
+    float* Kag = nullptr;      // [2][nv][nv+nb] top rows of K_n^-1 and K_0^-1 (agent level)
     double* Kinv64 = nullptr;  // [kdim][kdim]
     float* Ktop = nullptr;     // [n nv][kdim]
     int kp = 0;                // padded row length (multiple of 4) of the tensor-core operands
@@ -124,6 +125,7 @@ struct amto_plan_s {
     int last_batch = 0;
     bool fused = false;        // K^-1 applied per instance inside the pair kernel
     bool block = false;        // the loop runs in the one-block-per-instance solver
+    bool kron = false;         // K^-1 applied in its exact agent-structured form
     cudaStream_t cap_stream = nullptr;
     std::map<int, amto::Graph> graphs;
 

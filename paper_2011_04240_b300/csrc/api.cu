@@ -53,7 +53,7 @@ void free_plan(amto_plan_s* pl) {
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     pl->graphs.clear();
-    void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kinv64, pl->Ktop,
+    void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kag, pl->Kinv64, pl->Ktop,
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
@@ -174,15 +174,15 @@ amto_status validate_params(const amto_params& p) {
     if (p.precision < AMTO_PREC_FP32 || p.precision > AMTO_PREC_BF16)
         return einval("precision must be one of AMTO_PREC_*");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
-    if (p.apply_mode < AMTO_APPLY_AUTO || p.apply_mode > AMTO_APPLY_FUSED)
+    if (p.apply_mode < AMTO_APPLY_AUTO || p.apply_mode > AMTO_APPLY_KRONECKER)
         return einval("apply_mode must be one of AMTO_APPLY_*");
     if (p.apply_mode == AMTO_APPLY_FUSED && p.precision != AMTO_PREC_FP32)
         return einval("the fused apply is float32 (AMTO_PREC_FP32) only");
     if (p.loop_mode < AMTO_LOOP_AUTO || p.loop_mode > AMTO_LOOP_BLOCK)
         return einval("loop_mode must be one of AMTO_LOOP_*");
-    if (p.loop_mode == AMTO_LOOP_BLOCK &&
+    if (p.loop_mode == AMTO_LOOP_BLOCK && p.apply_mode != AMTO_APPLY_KRONECKER &&
         (p.precision != AMTO_PREC_FP32 || p.apply_mode == AMTO_APPLY_FUSED))
-        return einval("the block solver is float32 with the batched apply only");
+        return einval("the block solver applies K^-1 in float32 (dense or structured) only");
     if (p.tile_group != 0 && p.tile_group != 8 && p.tile_group != 16 && p.tile_group != 32)
         return einval("tile_group must be 0 (automatic), 8, 16 or 32");
     if (p.tile_time_blocks < 0 || p.tile_time_blocks > 8)
@@ -242,6 +242,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch);
     pl->fused = apply_fused(p);
+    pl->kron = p.apply_mode == AMTO_APPLY_KRONECKER;
     pl->block = loop_block(p);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
     pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
@@ -262,6 +263,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->Q32, (size_t)nv * nv);
     ALLOC(pl->A32, (size_t)nb * nv);
     ALLOC(pl->E0, (size_t)nv * nb);
+    ALLOC(pl->Kag, (size_t)2 * nv * (nv + nb));
     ALLOC(pl->Kinv64, (size_t)kdim * kdim);
     ALLOC(pl->Ktop, nvn * kdim);
     if (tc && !bf) {
@@ -405,7 +407,8 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
     out->launches_fixed = 4;
     out->time_blocks = plan->geo.QW;
-    out->apply_mode = plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
+    out->apply_mode = plan->kron ? AMTO_APPLY_KRONECKER
+                    : plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
     out->loop_mode = plan->block ? AMTO_LOOP_BLOCK : AMTO_LOOP_GRAPH;
     if (plan->block) {
         out->launches_per_iteration = 0;

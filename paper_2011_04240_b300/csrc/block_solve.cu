@@ -23,6 +23,7 @@
 
 #include "amto_internal.cuh"
 #include "schedule.cuh"
+#include "structured.cuh"
 
 namespace amto {
 namespace {
@@ -53,6 +54,8 @@ struct BlockGroup {
     const float* Q;      // [nv][nv]
     const float* Am;     // [nb][nv]
     const float* Kt;     // [n nv][kdim] K^-1_top
+    const float* Kag;    // [2][nv][nv+nb] agent-level inverse blocks (structured apply)
+    int kron;            // 1: structured apply instead of the dense product
     const float* beq;    // [B][3][n nb]
     const float* gpart;  // [B][NCb][3][n nv] partials of the initial projection
     float* xi;           // [B][3][n nv]
@@ -115,6 +118,7 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
     const int G = A.G, TB = 64 / G, S = A.S, S4 = S / 4, npad = A.npad, nbk = A.nbk;
     const int nTB = A.nTB, TCB = nTB * TB, MT = (m + TB - 1) / TB;
     __shared__ float red[kBT / 32];
+    __shared__ float kscr[64];
     __shared__ int s_flag;
     // shared memory plan
     float* xs = sm;                        // [3][n nv]   trajectories
@@ -192,9 +196,15 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
             rs[idx] = v;
         }
         __syncthreads();
+        if (A.kron) {  // structured: per agent 17 x 17 blocks, axis by axis
+            for (int ax = 0; ax < 3; ++ax) {
+                kron_apply_axis(rs + ax * kdim, n, nv, nb, A.Kag, xs + ax * nvn, kscr);
+                __syncthreads();
+            }
+        }
         // xi += K^-1_top [g; e]: a warp takes eight rows at a time, each lane
         // four columns per step, so 32 loads of K^-1 are in flight per lane
-        for (int r0 = warp * 8; r0 < nvn; r0 += (kBT / 32) * 8) {
+        for (int r0 = warp * 8; !A.kron && r0 < nvn; r0 += (kBT / 32) * 8) {
             float acc[8][3];
 #pragma unroll
             for (int rr = 0; rr < 8; ++rr) acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.f;
@@ -462,6 +472,8 @@ static BlockGroup block_group(const amto_plan_s* pl) {
     a.rinv = (float)(1.0 / pl->prm.rho);
     a.lam_floats = g.lam_floats;
     a.P = pl->P32; a.Q = pl->Q32; a.Am = pl->A32; a.Kt = pl->Ktop; a.beq = pl->beq;
+    a.Kag = pl->Kag;
+    a.kron = pl->kron ? 1 : 0;
     a.gpart = pl->gpart; a.xi = pl->xi; a.lam0 = pl->lam[0]; a.lam1 = pl->lam[1];
     a.iters = pl->iters; a.flags = pl->flags; a.rmax = pl->rmax; a.ctl = pl->ctl;
     return a;

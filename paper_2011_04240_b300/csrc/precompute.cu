@@ -104,13 +104,17 @@ __global__ void k_assemble(int n, int nv, int nb, double rho, const double* PtP,
 
 // Agent-level KKT matrix [[Pddot^T Pddot, A^T], [A, 0]] of the
 // smoothness-only initial solve.
-__global__ void k_assemble_agent(int nv, int nb, const double* DtD, const double* A, double* K) {
+// Agent-level KKT matrix [[DtD + w PtP, A^T], [A, 0]] (w = 0: smoothness only,
+// the ring of all agents moving together; w = rho n: the block of one agent
+// relative to the others, Remark 1's structure of the full matrix).
+__global__ void k_assemble_agent(int nv, int nb, const double* DtD, const double* PtP, double w,
+                                 const double* A, double* K) {
     int d = nv + nb;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= d * d) return;
     int r = idx / d, c = idx % d;
     double v = 0.0;
-    if (r < nv && c < nv) v = DtD[r * nv + c];
+    if (r < nv && c < nv) v = DtD[r * nv + c] + w * PtP[r * nv + c];
     else if (r < nv) v = A[(c - nv) * nv + r];
     else if (c < nv) v = A[(r - nv) * nv + c];
     K[idx] = v;
@@ -244,6 +248,13 @@ __global__ void k_split_top_bf16(int rows, int kdim, int ld, const double* Kinv,
     lo[idx] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
 }
 
+// Rows [0, nv) of an agent-level inverse as float32 [nv][nv + nb].
+__global__ void k_agent_top(int nv, int nb, const double* Kinv, float* out) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nv * (nv + nb)) return;
+    out[idx] = (float)Kinv[idx];
+}
+
 // E0 = rows [0, nv) and columns [nv, nv+nb) of the agent-level inverse.
 __global__ void k_extract_e0(int nv, int nb, const double* K0inv, float* E0) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,7 +298,7 @@ amto_status precompute(amto_plan_s* pl) {
     cudaStream_t s = pl->cap_stream;
     double *P = nullptr, *dP = nullptr, *ddP = nullptr, *PtP = nullptr, *DtD = nullptr,
            *A = nullptr, *K = nullptr, *W = nullptr, *K0 = nullptr, *K0inv = nullptr,
-           *sd = nullptr;
+           *Kn = nullptr, *Kninv = nullptr, *sd = nullptr;
     int* si = nullptr;
     unsigned long long* err = nullptr;
     amto_status st = AMTO_OK;
@@ -308,6 +319,8 @@ amto_status precompute(amto_plan_s* pl) {
     PC_ALLOC(W, sizeof(double) * (size_t)kdim * kdim * 2);
     PC_ALLOC(K0, sizeof(double) * (nv + nb) * (nv + nb));
     PC_ALLOC(K0inv, sizeof(double) * (nv + nb) * (nv + nb));
+    PC_ALLOC(Kn, sizeof(double) * (nv + nb) * (nv + nb));
+    PC_ALLOC(Kninv, sizeof(double) * (nv + nb) * (nv + nb));
     PC_ALLOC(sd, sizeof(double) * 4);
     PC_ALLOC(si, sizeof(int) * 4);
     PC_ALLOC(err, sizeof(unsigned long long));
@@ -319,13 +332,17 @@ amto_status precompute(amto_plan_s* pl) {
                                                       DtD, A);
         k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, nv, nb, pl->prm.rho,
                                                                        PtP, DtD, A, K);
-        k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(nv, nb, DtD, A, K0);
+        k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(nv, nb, DtD, PtP, 0.0,
+                                                                           A, K0);
+        k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(
+            nv, nb, DtD, PtP, pl->prm.rho * n, A, Kn);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("precompute kernel launch failed");
             st = AMTO_ECUDA;
         }
     }
     if (st == AMTO_OK) st = invert(nv + nb, K0, K0inv, W, si, sd, s);
+    if (st == AMTO_OK) st = invert(nv + nb, Kn, Kninv, W, si, sd, s);
     if (st == AMTO_OK) st = invert(kdim, K, pl->Kinv64, W, si, sd, s);
     if (st == AMTO_OK) {
         cudaMemsetAsync(err, 0, sizeof(unsigned long long), s);
@@ -360,6 +377,9 @@ amto_status precompute(amto_plan_s* pl) {
                 rows, kdim, pl->kp8, pl->Kinv64, reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi),
                 reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo));
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
+        k_agent_top<<<blocks(nv * (nv + nb), 64), 64, 0, s>>>(nv, nb, Kninv, pl->Kag);
+        k_agent_top<<<blocks(nv * (nv + nb), 64), 64, 0, s>>>(nv, nb, K0inv,
+                                                              pl->Kag + nv * (nv + nb));
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);
         k_to_f32<<<blocks(nb * nv, 128), 128, 0, s>>>((long long)nb * nv, A, pl->A32);
@@ -370,7 +390,8 @@ amto_status precompute(amto_plan_s* pl) {
         }
     }
     cudaFree(P); cudaFree(dP); cudaFree(ddP); cudaFree(PtP); cudaFree(DtD); cudaFree(A);
-    cudaFree(K); cudaFree(W); cudaFree(K0); cudaFree(K0inv); cudaFree(sd); cudaFree(si);
+    cudaFree(K); cudaFree(W); cudaFree(K0); cudaFree(K0inv); cudaFree(Kn); cudaFree(Kninv);
+    cudaFree(sd); cudaFree(si);
     cudaFree(err);
     return st;
 }

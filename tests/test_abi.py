@@ -57,7 +57,7 @@ def _params(**kw):
                                  dict(precision=9), dict(tile_group=12), dict(tile_group=4),
                                  dict(tile_time_blocks=-1), dict(tile_time_blocks=9),
                                  dict(n_agents=256, tile_group=8, tile_time_blocks=8),
-                                 dict(apply_mode=3), dict(apply_mode=-1),
+                                 dict(apply_mode=4), dict(apply_mode=-1),
                                  dict(apply_mode=2, precision=1), dict(loop_mode=3),
                                  dict(loop_mode=2, precision=1), dict(loop_mode=2, apply_mode=2)])
 def test_create_rejects_invalid_params(lib, bad):
