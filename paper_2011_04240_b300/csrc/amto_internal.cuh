@@ -30,6 +30,46 @@ void clear_error();
 inline bool prec_tc(int p) { return p != AMTO_PREC_FP32; }
 inline bool prec_bf16(int p) { return p == AMTO_PREC_BF16X3 || p == AMTO_PREC_BF16; }
 
+// Programmatic dependent launch: the loop's kernels are launched so that the
+// next one can be scheduled while the previous one drains; each of them waits
+// here for its predecessor's results before touching global memory (a no-op
+// when launched without the attribute).
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+inline cudaError_t launch_pdl_c(const void* fn, dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t s, void** args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // Flags per instance (device int).
 enum : int { FLAG_DONE = 1, FLAG_APPLY = 2, FLAG_NONFINITE = 4 };
 

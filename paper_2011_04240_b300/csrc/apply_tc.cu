@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long bars[2 * kTcStages + 1];
     __shared__ unsigned tmem_slot;
+    griddep_wait();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, kz = blockIdx.z;
     constexpr int kBK = BF ? kRowBytes / 2 : kRowBytes / 4;  // K elements per k-block
@@ -352,11 +353,11 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     tc_shape(pl, batch, &tm, &tn, &sp, &a.kper);
     a.splits = sp;
     if (prec_bf16(pl->prm.precision))
-        k_apply_tc<true><<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(
-            pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a);
+        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<true>, dim3(tm, tn, sp), dim3(128), tc_smem_bytes(), s,
+                                 pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a));
     else
-        k_apply_tc<false><<<dim3(tm, tn, sp), 128, tc_smem_bytes(), s>>>(
-            pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a);
+        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<false>, dim3(tm, tn, sp), dim3(128), tc_smem_bytes(), s,
+                                 pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a));
     AMTO_CUDA_TRY(cudaGetLastError());
     if (sp > 1) return launch_splitk_reduce(pl, batch, sp, s);
     return AMTO_OK;
