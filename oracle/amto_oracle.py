@@ -51,6 +51,12 @@ Readings of ambiguous passages (each also listed in the design notes):
             largest Euclidean norm of f_c over all pairs and samples; the
             iteration count is the number of QP solves.
   R-degen   Delta = 0: atan2(0,0) = 0, so alpha = beta = 0.
+  R-rho-sched  Sec. IV-A uses 10 increasing rho values, the larger ones in
+            the later iterations, without giving the values or the switch:
+            rho_j = rho_0 g^j (j = 0..J-1) and QP solve k (k >= 1) belongs to
+            stage min(J-1, (k-1) div E); iteration k runs entirely with rho_k
+            (the target b of Eq. b_f, the d step and the lambda update), and
+            lambda carries over unchanged across a switch.
 """
 from __future__ import annotations
 
@@ -338,6 +344,29 @@ def solve(M: Matrices, start, goal, max_iters: int, tol: float = 0.0,
     st = init_state(M, beq, mode) if state is None else state
     while st.k < max_iters:
         st = am_iteration(M, st, beq, mode, increment)
+        if history is not None:
+            history.append(st.r_max)
+        if st.r_max < tol:
+            break
+    return st
+
+
+def rho_stage(k: int, n_stages: int, stage_iters: int) -> int:
+    """Stage of QP solve k (k >= 1) in the increasing-rho schedule (R-rho-sched)."""
+    return min(n_stages - 1, (k - 1) // stage_iters)
+
+
+def solve_schedule(Ms: list, stage_iters: int, start, goal, max_iters: int, tol: float = 0.0,
+                   mode: str = "R2", history: list | None = None) -> State:
+    """Algorithm 1 with the increasing penalty of Sec. IV-A (reading
+    R-rho-sched): `Ms` holds the matrices (cached inverses) of the stages in
+    increasing rho; iteration k uses Ms[rho_stage(k)].  Same loop and stopping
+    rule as `solve`."""
+    beq = boundary_values(start, goal, Ms[0].bc_mask)
+    st = init_state(Ms[0], beq, mode)
+    while st.k < max_iters:
+        M = Ms[rho_stage(st.k + 1, len(Ms), stage_iters)]
+        st = am_iteration(M, st, beq, mode)
         if history is not None:
             history.append(st.r_max)
         if st.r_max < tol:
