@@ -97,6 +97,17 @@ typedef struct {
     int tile_time_blocks;
     int apply_mode;    /* AMTO_APPLY_*: where the cached inverse is applied */
     int loop_mode;     /* AMTO_LOOP_*: how the iterations are driven */
+    /* Increasing penalty (Sec. IV-A: several rho values, the larger ones in
+     * later iterations; values and switch are this library's reading):
+     * rho_j = rho * rho_growth^j for j < rho_stages, QP solve k >= 1 uses
+     * stage min(rho_stages - 1, (k - 1) / rho_stage_iters), the multipliers
+     * carry over.  One cached inverse per stage.  rho_stages 0 or 1: constant
+     * rho.  A batch iterates in step (every instance of a solve is at the same
+     * k), so the stages switch for the whole batch; the serving layer uses a
+     * constant rho. */
+    int rho_stages;        /* 0..16 */
+    double rho_growth;     /* > 0 when rho_stages > 1 */
+    int rho_stage_iters;   /* >= 1 when rho_stages > 1 */
 } amto_params;
 
 /* How the loop of Algorithm 1 runs.  GRAPH: one CUDA graph per batch size,

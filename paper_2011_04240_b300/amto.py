@@ -42,7 +42,9 @@ class Params(ctypes.Structure):
                 ("bc_mask", ctypes.c_uint), ("proj_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
-                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int)]
+                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
+                ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
+                ("rho_stage_iters", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -249,13 +251,14 @@ class Planner:
                  rho: float = 1.0, poly_degree: int = 10, bc_mask: int = BC_ALL,
                  proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
-                 apply_mode: int = 0, loop_mode: int = 0):
+                 apply_mode: int = 0, loop_mode: int = 0, rho_stages: int = 0,
+                 rho_growth: float = 1.0, rho_stage_iters: int = 1):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
-                             apply_mode, loop_mode)
+                             apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)

@@ -85,6 +85,23 @@ struct Ctl {
     unsigned int loop_count;    // pair-kernel passes of this solve (loop guard)
     unsigned int active_last;   // instances still iterating after the last pass
     unsigned int error;         // nonzero: a bounded device wait ran out
+    int stage;                  // rho stage of the next QP solve (the batch iterates in step)
+};
+
+// Increasing-rho schedule (Sec. IV-A): rho_j = rho_0 g^j, j < J; QP solve k
+// (k >= 1) belongs to stage min(J - 1, (k - 1) / E); k = 0 (the initial
+// projection, lambda = 0) to stage 0.
+constexpr int kMaxRhoStages = 16;
+__host__ __device__ inline int rho_stage_of(int k, int J, int E) {
+    if (k < 1) return 0;
+    const int s = (k - 1) / E;
+    return s < J - 1 ? s : J - 1;
+}
+struct RhoSched {
+    int J, E;
+    float rho[kMaxRhoStages];
+    float rinv[kMaxRhoStages];   // float(1 / rho) computed in double
+    double rho_d[kMaxRhoStages];
 };
 
 // Geometry of the pair kernel's work decomposition (see iterate.cu).
@@ -140,7 +157,10 @@ struct amto_plan_s {
     int kp8 = 0;               // padded row length (multiple of 8) of the BF16 operands
     unsigned short* Kb_hi = nullptr;  // [n nv][kp8] BF16(K^-1_top) (BF16 modes)
     unsigned short* Kb_lo = nullptr;  // [n nv][kp8] BF16(K^-1_top - Kb_hi)
-    CUtensorMap tm_a_hi, tm_a_lo, tm_b_hi, tm_b_lo;  // TMA descriptors (64-byte aligned type)
+    CUtensorMap tm_a_hi[amto::kMaxRhoStages], tm_a_lo[amto::kMaxRhoStages];  // K^-1 per rho stage
+    CUtensorMap tm_b_hi, tm_b_lo;  // right-hand-side operands (TMA descriptors, 64-byte aligned)
+    amto::RhoSched sched;      // rho stages (J = 1: constant rho)
+    size_t ks_top = 0, ks_tc = 0, ks_bf = 0, ks_ag = 0;  // per-stage strides of the inverses
 
     // state for max_batch instances (device)
     float* xi = nullptr;       // [B][3][n nv]

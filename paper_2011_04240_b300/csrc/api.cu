@@ -178,6 +178,16 @@ amto_status validate_params(const amto_params& p) {
         return einval("apply_mode must be one of AMTO_APPLY_*");
     if (p.apply_mode == AMTO_APPLY_FUSED && p.precision != AMTO_PREC_FP32)
         return einval("the fused apply is float32 (AMTO_PREC_FP32) only");
+    if (p.rho_stages < 0 || p.rho_stages > kMaxRhoStages)
+        return einval("rho_stages must be in [0, 16]");
+    if (p.rho_stages > 1 && (!(p.rho_growth > 0) || !std::isfinite(p.rho_growth) ||
+                             p.rho_stage_iters < 1))
+        return einval("an increasing-rho schedule needs rho_growth > 0 and rho_stage_iters >= 1");
+    if (p.rho_stages > 1) {
+        const double last = p.rho * std::pow(p.rho_growth, p.rho_stages - 1);
+        if (!(last > 0) || !std::isfinite(last) || last > 1e8)
+            return einval("the last rho stage must be a finite positive value <= 1e8");
+    }
     if (p.loop_mode < AMTO_LOOP_AUTO || p.loop_mode > AMTO_LOOP_BLOCK)
         return einval("loop_mode must be one of AMTO_LOOP_*");
     if (p.loop_mode == AMTO_LOOP_BLOCK && p.apply_mode != AMTO_APPLY_KRONECKER &&
@@ -242,6 +252,18 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch);
     pl->fused = apply_fused(p);
+    {
+        RhoSched& sc = pl->sched;
+        sc.J = p.rho_stages > 1 ? p.rho_stages : 1;
+        sc.E = p.rho_stages > 1 ? p.rho_stage_iters : 1;
+        for (int j = 0; j < kMaxRhoStages; ++j) {
+            const double r = j < sc.J ? p.rho * std::pow(p.rho_stages > 1 ? p.rho_growth : 1.0, j)
+                                      : p.rho;
+            sc.rho_d[j] = r;
+            sc.rho[j] = (float)r;
+            sc.rinv[j] = (float)(1.0 / r);
+        }
+    }
     pl->kron = p.apply_mode == AMTO_APPLY_KRONECKER;
     pl->block = loop_block(p);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
@@ -263,17 +285,22 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->Q32, (size_t)nv * nv);
     ALLOC(pl->A32, (size_t)nb * nv);
     ALLOC(pl->E0, (size_t)nv * nb);
-    ALLOC(pl->Kag, (size_t)2 * nv * (nv + nb));
+    const int J = pl->sched.J;
+    pl->ks_ag = (size_t)2 * nv * (nv + nb);
+    pl->ks_top = nvn * kdim;
+    pl->ks_tc = nvn * pl->kp;
+    pl->ks_bf = nvn * pl->kp8;
+    ALLOC(pl->Kag, J * pl->ks_ag);
     ALLOC(pl->Kinv64, (size_t)kdim * kdim);
-    ALLOC(pl->Ktop, nvn * kdim);
+    ALLOC(pl->Ktop, J * pl->ks_top);
     if (tc && !bf) {
-        ALLOC(pl->Kt_hi, nvn * pl->kp);
-        ALLOC(pl->Kt_lo, nvn * pl->kp);
+        ALLOC(pl->Kt_hi, J * pl->ks_tc);
+        ALLOC(pl->Kt_lo, J * pl->ks_tc);
         ALLOC(pl->rhs_lo, (size_t)B * 3 * pl->kp);
     }
     if (bf) {
-        ALLOC(pl->Kb_hi, nvn * pl->kp8);
-        ALLOC(pl->Kb_lo, nvn * pl->kp8);
+        ALLOC(pl->Kb_hi, J * pl->ks_bf);
+        ALLOC(pl->Kb_lo, J * pl->ks_bf);
         ALLOC(pl->rb_hi, (size_t)B * 3 * pl->kp8);
         ALLOC(pl->rb_lo, (size_t)B * 3 * pl->kp8);
     }

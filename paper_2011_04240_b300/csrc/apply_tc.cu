@@ -121,15 +121,26 @@ struct TcArgs {
     Ctl* ctl;
 };
 
+// Tensor maps of the K^-1 operands of every rho stage and of the right-hand
+// sides (kernel parameters: the descriptors must live in parameter space).
+struct TcMaps {
+    CUtensorMap a_hi[kMaxRhoStages];
+    CUtensorMap a_lo[kMaxRhoStages];
+    CUtensorMap b_hi, b_lo;
+};
+
 template <bool BF>
 __global__ void __launch_bounds__(128, 1)
-    k_apply_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-               TcArgs A) {
+    k_apply_tc(const __grid_constant__ TcMaps TM, TcArgs A) {
     extern __shared__ unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long bars[2 * kTcStages + 1];
     __shared__ unsigned tmem_slot;
     griddep_wait();
+    const int stage = A.ctl->stage;  // rho stage of this QP solve (the batch is in step)
+    const CUtensorMap& ta_hi = TM.a_hi[stage];
+    const CUtensorMap& ta_lo = TM.a_lo[stage];
+    const CUtensorMap& tb_hi = TM.b_hi;
+    const CUtensorMap& tb_lo = TM.b_lo;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, kz = blockIdx.z;
     constexpr int kBK = BF ? kRowBytes / 2 : kRowBytes / 4;  // K elements per k-block
@@ -308,18 +319,25 @@ amto_status tc_configure(amto_plan_s* pl) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes()));
     const int M = pl->n * pl->nv, K = pl->kdim, rows_b = 3 * pl->prm.max_batch;
-    amto_status st;
-    if (prec_bf16(pl->prm.precision)) {
-        st = make_map(&pl->tm_a_hi, pl->Kb_hi, M, K, pl->kp8, true);
-        if (st == AMTO_OK) st = make_map(&pl->tm_a_lo, pl->Kb_lo, M, K, pl->kp8, true);
-        if (st == AMTO_OK) st = make_map(&pl->tm_b_hi, pl->rb_hi, rows_b, K, pl->kp8, true);
-        if (st == AMTO_OK) st = make_map(&pl->tm_b_lo, pl->rb_lo, rows_b, K, pl->kp8, true);
-    } else {
-        st = make_map(&pl->tm_a_hi, pl->Kt_hi, M, K, pl->kp, false);
-        if (st == AMTO_OK) st = make_map(&pl->tm_a_lo, pl->Kt_lo, M, K, pl->kp, false);
-        if (st == AMTO_OK) st = make_map(&pl->tm_b_hi, pl->rhs, rows_b, K, pl->kp, false);
-        if (st == AMTO_OK) st = make_map(&pl->tm_b_lo, pl->rhs_lo, rows_b, K, pl->kp, false);
+    amto_status st = AMTO_OK;
+    const bool bf = prec_bf16(pl->prm.precision);
+    for (int j = 0; j < pl->sched.J && st == AMTO_OK; ++j) {
+        if (bf) {
+            st = make_map(&pl->tm_a_hi[j], pl->Kb_hi + j * pl->ks_bf, M, K, pl->kp8, true);
+            if (st == AMTO_OK)
+                st = make_map(&pl->tm_a_lo[j], pl->Kb_lo + j * pl->ks_bf, M, K, pl->kp8, true);
+        } else {
+            st = make_map(&pl->tm_a_hi[j], pl->Kt_hi + j * pl->ks_tc, M, K, pl->kp, false);
+            if (st == AMTO_OK)
+                st = make_map(&pl->tm_a_lo[j], pl->Kt_lo + j * pl->ks_tc, M, K, pl->kp, false);
+        }
     }
+    if (st == AMTO_OK)
+        st = bf ? make_map(&pl->tm_b_hi, pl->rb_hi, rows_b, K, pl->kp8, true)
+                : make_map(&pl->tm_b_hi, pl->rhs, rows_b, K, pl->kp, false);
+    if (st == AMTO_OK)
+        st = bf ? make_map(&pl->tm_b_lo, pl->rb_lo, rows_b, K, pl->kp8, true)
+                : make_map(&pl->tm_b_lo, pl->rhs_lo, rows_b, K, pl->kp, false);
     return st;
 }
 
@@ -349,15 +367,23 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     a.flags = pl->flags;
     a.ws = pl->gemm_ws;
     a.ctl = pl->ctl;
-    int tm, tn, sp;
-    tc_shape(pl, batch, &tm, &tn, &sp, &a.kper);
+    int tm_, tn, sp;
+    tc_shape(pl, batch, &tm_, &tn, &sp, &a.kper);
     a.splits = sp;
+    static_assert(sizeof(TcMaps) + sizeof(TcArgs) < 32000, "kernel parameter space");
+    TcMaps tm;
+    for (int j = 0; j < kMaxRhoStages; ++j) {
+        tm.a_hi[j] = pl->tm_a_hi[j < pl->sched.J ? j : 0];
+        tm.a_lo[j] = pl->tm_a_lo[j < pl->sched.J ? j : 0];
+    }
+    tm.b_hi = pl->tm_b_hi;
+    tm.b_lo = pl->tm_b_lo;
     if (prec_bf16(pl->prm.precision))
-        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<true>, dim3(tm, tn, sp), dim3(128), tc_smem_bytes(), s,
-                                 pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a));
+        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<true>, dim3(tm_, tn, sp), dim3(128), tc_smem_bytes(),
+                                 s, tm, a));
     else
-        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<false>, dim3(tm, tn, sp), dim3(128), tc_smem_bytes(), s,
-                                 pl->tm_a_hi, pl->tm_a_lo, pl->tm_b_hi, pl->tm_b_lo, a));
+        AMTO_CUDA_TRY(launch_pdl(k_apply_tc<false>, dim3(tm_, tn, sp), dim3(128), tc_smem_bytes(),
+                                 s, tm, a));
     AMTO_CUDA_TRY(cudaGetLastError());
     if (sp > 1) return launch_splitk_reduce(pl, batch, sp, s);
     return AMTO_OK;

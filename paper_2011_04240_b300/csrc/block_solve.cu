@@ -48,13 +48,15 @@ __host__ __device__ inline size_t block_tb_floats(int n, int nv, int npad, int T
 
 struct BlockGroup {
     int n, m, nv, nb, kdim, G, nbk, npad, S, nTB, NCb, literal;
-    float ia2, ib2, bz, rho, rinv;
+    float ia2, ib2, bz;
+    RhoSched sch;        // penalty per stage; iteration k uses stage rho_stage_of(k)
+    size_t ks_top, ks_ag;  // elements between the stages of Kt and Kag
     long long lam_floats;
     const float* P;      // [m][nv] float32 basis
     const float* Q;      // [nv][nv]
     const float* Am;     // [nb][nv]
-    const float* Kt;     // [n nv][kdim] K^-1_top
-    const float* Kag;    // [2][nv][nv+nb] agent-level inverse blocks (structured apply)
+    const float* Kt;     // [stages][n nv][kdim] K^-1_top
+    const float* Kag;    // [stages][2][nv][nv+nb] agent-level inverse blocks (structured apply)
     int kron;            // 1: structured apply instead of the dense product
     const float* beq;    // [B][3][n nb]
     const float* gpart;  // [B][NCb][3][n nv] partials of the initial projection
@@ -74,10 +76,12 @@ struct BlockArgs {
 };
 
 // The batched kernel's pair arithmetic for one sample (lane orientation):
-// projection, d step, f_c, multiplier update, |f_c|^2 and tt = f_c + lambda/rho.
+// projection, d step, f_c, multiplier update, |f_c|^2 and tt = f_c + lambda/rho'
+// (rho' the penalty of the next QP solve).
 template <bool LIT>
 __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float sgb, float ia2,
-                                           float ib2, float rho, float rinv, float& l0, float& l1,
+                                           float ib2, float rho, float rinv, float rnx,
+                                           float& l0, float& l1,
                                            float& l2, float& t0, float& t1, float& t2,
                                            float& fsq) {
     const float s2 = __fmaf_rn(__fmul_rn(dz, dz), ib2,
@@ -106,9 +110,9 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
     l1 = __fmaf_rn(rho, fy, l1);
     l2 = __fmaf_rn(rho, fz, l2);
     fsq = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
-    t0 = __fmaf_rn(l0, rinv, fx);
-    t1 = __fmaf_rn(l1, rinv, fy);
-    t2 = __fmaf_rn(l2, rinv, fz);
+    t0 = __fmaf_rn(l0, rnx, fx);
+    t1 = __fmaf_rn(l1, rnx, fy);
+    t2 = __fmaf_rn(l2, rnx, fz);
 }
 
 template <bool LIT>
@@ -177,6 +181,12 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
     __syncthreads();
 
     for (int guard = 0; guard <= A.ctl->max_iters + 1; ++guard) {
+        // this pass solves QP k_it and closes it; the target it leaves feeds QP k_it + 1
+        const int sc = rho_stage_of(k_it, A.sch.J, A.sch.E);
+        const int sn = rho_stage_of(k_it + 1, A.sch.J, A.sch.E);
+        const float rho = A.sch.rho[sc], rinv = A.sch.rinv[sc], rnx = A.sch.rinv[sn];
+        const float* Kt = A.Kt + (size_t)sc * A.ks_top;
+        const float* Kag = A.Kag + (size_t)sc * A.ks_ag;
         // right-hand side (increment form)
         for (int idx = tid; idx < 3 * kdim; idx += kBT) {
             const int ax = idx / kdim, row = idx % kdim;
@@ -186,7 +196,7 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
                 const int i = row / nv, k = row % nv;
                 float q = 0.f;
                 for (int j = 0; j < nv; ++j) q = fmaf(A.Q[k * nv + j], xr[i * nv + j], q);
-                v = fmaf(A.rho, gs[ax * nvn + row], -q);
+                v = fmaf(rho, gs[ax * nvn + row], -q);
             } else {
                 const int r0 = row - nvn, i = r0 / nb, rr = r0 % nb;
                 float e = 0.f;
@@ -198,7 +208,7 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
         __syncthreads();
         if (A.kron) {  // structured: per agent 17 x 17 blocks, axis by axis
             for (int ax = 0; ax < 3; ++ax) {
-                kron_apply_axis(rs + ax * kdim, n, nv, nb, A.Kag, xs + ax * nvn, kscr);
+                kron_apply_axis(rs + ax * kdim, n, nv, nb, Kag, xs + ax * nvn, kscr);
                 __syncthreads();
             }
         }
@@ -215,7 +225,7 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int c = c0 + lane + 32 * j, r = r0 + rr;
-                        kv[rr][j] = (r < nvn && c < kdim) ? __ldg(A.Kt + (size_t)r * kdim + c) : 0.f;
+                        kv[rr][j] = (r < nvn && c < kdim) ? __ldg(Kt + (size_t)r * kdim + c) : 0.f;
                     }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -327,7 +337,7 @@ __device__ void solve_instance(const BlockGroup& A, int b, float* sm) {
                         float l0 = lv[u][0], l1 = lv[u][1], l2 = lv[u][2];
                         const float sgb = o < pp ? A.bz : -A.bz;
                         float fsq;
-                        pair_step1<LIT>(dx, dy, dz, sgb, A.ia2, A.ib2, A.rho, A.rinv, l0, l1, l2,
+                        pair_step1<LIT>(dx, dy, dz, sgb, A.ia2, A.ib2, rho, rinv, rnx, l0, l1, l2,
                                         t0v, t1v, t2v, fsq);
                         lout[li[u]] = l0;
                         lout[li[u] + 256] = l1;
@@ -468,8 +478,9 @@ static BlockGroup block_group(const amto_plan_s* pl) {
     a.ia2 = (float)(1.0 / (pl->prm.a * pl->prm.a));
     a.ib2 = (float)(1.0 / (pl->prm.b * pl->prm.b));
     a.bz = (float)pl->prm.b;
-    a.rho = (float)pl->prm.rho;
-    a.rinv = (float)(1.0 / pl->prm.rho);
+    a.sch = pl->sched;
+    a.ks_top = pl->ks_top;
+    a.ks_ag = pl->ks_ag;
     a.lam_floats = g.lam_floats;
     a.P = pl->P32; a.Q = pl->Q32; a.Am = pl->A32; a.Kt = pl->Ktop; a.beq = pl->beq;
     a.Kag = pl->Kag;

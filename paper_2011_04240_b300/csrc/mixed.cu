@@ -166,6 +166,13 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, a
                       "m_steps, poly_degree, T, a, b, rho, bc_mask and proj_mode");
             return AMTO_EINVAL;
         }
+        bool same_sched = a->sched.J == z->sched.J && a->sched.E == z->sched.E;
+        for (int j = 0; same_sched && j < a->sched.J; ++j)
+            same_sched = a->sched.rho_d[j] == z->sched.rho_d[j];
+        if (!same_sched) {  // one loop count drives every group's penalty stage
+            set_error("invalid argument: the plans of a mixed batch must share the rho schedule");
+            return AMTO_EINVAL;
+        }
         for (int h = 0; h < g; ++h)
             if (plans[h] == a) {
                 set_error("invalid argument: a plan appears twice");

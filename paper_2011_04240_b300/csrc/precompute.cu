@@ -330,21 +330,31 @@ amto_status precompute(amto_plan_s* pl) {
         k_basis<<<blocks(m * nv, 128), 128, 0, s>>>(m, N, pl->prm.T, P, dP, ddP);
         k_small<<<blocks(nv * nv, 128), 128, 0, s>>>(m, nv, pl->prm.bc_mask, P, dP, ddP, PtP,
                                                       DtD, A);
-        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, nv, nb, pl->prm.rho,
-                                                                       PtP, DtD, A, K);
         k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(nv, nb, DtD, PtP, 0.0,
                                                                            A, K0);
-        k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(
-            nv, nb, DtD, PtP, pl->prm.rho * n, A, Kn);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("precompute kernel launch failed");
             st = AMTO_ECUDA;
         }
     }
     if (st == AMTO_OK) st = invert(nv + nb, K0, K0inv, W, si, sd, s);
-    if (st == AMTO_OK) st = invert(nv + nb, Kn, Kninv, W, si, sd, s);
-    if (st == AMTO_OK) st = invert(kdim, K, pl->Kinv64, W, si, sd, s);
-    if (st == AMTO_OK) {
+    // one cached inverse per rho stage (Remarks 1-2: K depends on rho and n
+    // only); the last one computed, stage 0, stays in Kinv64
+    const int rows = n * nv, d = nv + nb;
+    double worst = 0.0;
+    for (int j = pl->sched.J - 1; j >= 0 && st == AMTO_OK; --j) {
+        const double rho = pl->sched.rho_d[j];
+        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, nv, nb, rho, PtP, DtD,
+                                                                       A, K);
+        k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * n, A, Kn);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("precompute kernel launch failed");
+            st = AMTO_ECUDA;
+            break;
+        }
+        st = invert(nv + nb, Kn, Kninv, W, si, sd, s);
+        if (st == AMTO_OK) st = invert(kdim, K, pl->Kinv64, W, si, sd, s);
+        if (st != AMTO_OK) break;
         cudaMemsetAsync(err, 0, sizeof(unsigned long long), s);
         k_check<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(kdim, K, pl->Kinv64, err);
         unsigned long long bits = 0;
@@ -352,34 +362,37 @@ amto_status precompute(amto_plan_s* pl) {
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             set_error("precompute self-check failed to run");
             st = AMTO_ECUDA;
-        } else {
-            double e;
-            memcpy(&e, &bits, sizeof(e));
-            pl->kkt_check = e;
-            if (!(e < 1e-6)) {
-                char buf[160];
-                snprintf(buf, sizeof(buf), "KKT inverse self-check failed: max|K K^-1 - I| = %g", e);
-                set_error(buf);
-                st = AMTO_ENUMERIC;
-            }
+            break;
         }
-    }
-    if (st == AMTO_OK) {
-        const int rows = n * nv;
+        double e;
+        memcpy(&e, &bits, sizeof(e));
+        worst = e > worst ? e : worst;
+        if (!(e < 1e-6)) {
+            char buf[160];
+            snprintf(buf, sizeof(buf), "KKT inverse self-check failed: max|K K^-1 - I| = %g", e);
+            set_error(buf);
+            st = AMTO_ENUMERIC;
+            break;
+        }
         // top n*nv rows of the row-major inverse are its first rows*kdim entries
-        k_to_f32<<<blocks((long long)rows * kdim, 256), 256, 0, s>>>((long long)rows * kdim,
-                                                                     pl->Kinv64, pl->Ktop);
+        k_to_f32<<<blocks((long long)rows * kdim, 256), 256, 0, s>>>(
+            (long long)rows * kdim, pl->Kinv64, pl->Ktop + j * pl->ks_top);
         if (pl->Kt_hi)
             k_split_top<<<blocks((long long)rows * pl->kp, 256), 256, 0, s>>>(
-                rows, kdim, pl->kp, pl->Kinv64, pl->Kt_hi, pl->Kt_lo);
+                rows, kdim, pl->kp, pl->Kinv64, pl->Kt_hi + j * pl->ks_tc,
+                pl->Kt_lo + j * pl->ks_tc);
         if (pl->Kb_hi)
             k_split_top_bf16<<<blocks((long long)rows * pl->kp8, 256), 256, 0, s>>>(
-                rows, kdim, pl->kp8, pl->Kinv64, reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi),
-                reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo));
+                rows, kdim, pl->kp8, pl->Kinv64,
+                reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi) + j * pl->ks_bf,
+                reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo) + j * pl->ks_bf);
+        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, Kninv, pl->Kag + j * pl->ks_ag);
+        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, K0inv,
+                                                      pl->Kag + j * pl->ks_ag + nv * d);
+    }
+    pl->kkt_check = worst;
+    if (st == AMTO_OK) {
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
-        k_agent_top<<<blocks(nv * (nv + nb), 64), 64, 0, s>>>(nv, nb, Kninv, pl->Kag);
-        k_agent_top<<<blocks(nv * (nv + nb), 64), 64, 0, s>>>(nv, nb, K0inv,
-                                                              pl->Kag + nv * (nv + nb));
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);
         k_to_f32<<<blocks(nb * nv, 128), 128, 0, s>>>((long long)nb * nv, A, pl->A32);

@@ -139,6 +139,10 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     v.P32 = pl.P32; v.P64 = pl.P64; v.Q32 = pl.Q32; v.A32 = pl.A32; v.E0 = pl.E0;
     v.Kinv64 = pl.Kinv64; v.Ktop = pl.Ktop; v.kp = pl.kp;
     v.fused = pl.fused;
+    v.kron = pl.kron;
+    v.Kag = pl.Kag;
+    v.sched = pl.sched;
+    v.ks_top = pl.ks_top; v.ks_ag = pl.ks_ag;
     v.xi = reinterpret_cast<float*>(base + o_xi);
     v.beq = reinterpret_cast<float*>(base + o_beq);
     v.lam[0] = reinterpret_cast<float*>(base + o_lam0);
