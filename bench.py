@@ -289,14 +289,17 @@ def cpu_baseline_oracle(prob, seconds=12.0, mode="R3"):
                       f"{dt:.1f} s, FP64 numpy/scipy"}
 
 
-def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
+def plain_per_instance(seeds=(0, 1, 2, 3, 4), rho_schedule=None):
     """Plain FP32 per-instance GPU solve: 16 agents, 6x6x3 m box, m = 100,
-    iterate to max residual < 1e-2 or 500 iterations, one instance at a time."""
+    iterate to max residual < 1e-2 or 500 iterations, one instance at a time.
+    `rho_schedule` = (stages, growth, solves per stage) runs the increasing
+    penalty of Sec. IV-A instead of the constant rho = 1."""
     import numpy as np
     import torch
     import workloads as W
     from paper_2011_04240_b300 import Planner
-    pl = Planner(16, 100, 8.0, max_batch=1)
+    J, g, E = rho_schedule if rho_schedule else (0, 1.0, 1)
+    pl = Planner(16, 100, 8.0, max_batch=1, rho_stages=J, rho_growth=g, rho_stage_iters=E)
     lat, its, res = [], [], []
     for rep in range(2):
         for sd in seeds:
@@ -315,7 +318,10 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4)):
                 res.append(float(r.item()))
     pl.close()
     lat = np.array(lat)
-    return {"workload": "16 agents, 6x6x3 m box, m=100, tol 1e-2 / 500 iterations, batch 1",
+    wl = "16 agents, 6x6x3 m box, m=100, tol 1e-2 / 500 iterations, batch 1"
+    if rho_schedule:
+        wl += f", rho = {g:.4g}^j for j < {J}, {E} solves per stage"
+    return {"workload": wl,
             "value": float(sum(its) / (lat.sum() / 1e3)), "unit": UNIT,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "iterations": its, "final_resid_max": max(res)}
@@ -687,6 +693,8 @@ def main():
                                                           "apply": kms[2] / max(kcnt[2], 1)}}
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
+            extras["rho_schedule_per_instance"] = plain_per_instance(
+                rho_schedule=(10, 100 ** (1 / 9), 10))
             extras["config1_latency"] = config1_latency()
             extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])

@@ -108,7 +108,26 @@ typedef struct {
     int rho_stages;        /* 0..16 */
     double rho_growth;     /* > 0 when rho_stages > 1 */
     int rho_stage_iters;   /* >= 1 when rho_stages > 1 */
+    int multipliers;       /* AMTO_MULT_*: how lambda is kept between iterations */
 } amto_params;
+
+/* How the multipliers lambda (Eq. lag_update) are kept between iterations.
+ * PAIRS: one float per pair, sample and axis, as Algorithm 1 keeps them;
+ * every pair step reads and rewrites all of them (24 bytes per pair and
+ * sample).  AGGREGATE (AMTO_PROJ_NOLAMBDA plans in the graph loop with the
+ * batched or Kronecker apply): in that reading lambda enters an iteration
+ * only through b_fc (Eq. b_f), and b_fc only through A_fc^T b_fc in the
+ * right-hand side of Eq. kkt_step_x, which is linear in lambda; so the plan
+ * keeps L = A_fc^T lambda (3 n (N+1) floats per instance) and updates it with
+ * the same linear map, L_k = L_{k-1} + rho_k A_fc^T f_c^k.  The iterates are
+ * those of PAIRS in exact arithmetic (float32 rounding differs), and the
+ * pair step then reads and writes no per-pair state.  The per-pair
+ * multipliers of such a plan are never formed: amto_get_state returns
+ * EINVAL for lambda_out (alpha, beta and d, which this reading computes
+ * from Delta alone, are still returned).  A warm start's lambda_init is
+ * reduced to L once, in the solve's setup.  AUTO: AGGREGATE where allowed,
+ * else PAIRS. */
+enum { AMTO_MULT_AUTO = 0, AMTO_MULT_PAIRS = 1, AMTO_MULT_AGGREGATE = 2 };
 
 /* How the loop of Algorithm 1 runs.  GRAPH: one CUDA graph per batch size,
  * a conditional WHILE node around the iteration's kernels (right-hand side,
@@ -147,7 +166,8 @@ typedef struct {
     int group;                          /* agents per lane group of the pair kernel */
     int t_chunk;                        /* time samples per pair-kernel block */
     int n_chunks;                       /* pair-kernel blocks per instance */
-    long long lambda_floats;            /* float32 multiplier slots per instance (one buffer) */
+    long long lambda_floats;            /* float32 multiplier slots per instance (one buffer;
+                                           0 for AMTO_MULT_AGGREGATE plans) */
     double kkt_check;                   /* max |K K^-1 - I| of the FP64 inverse */
     size_t device_bytes;                /* device memory owned by the plan */
     int launches_per_iteration;         /* kernels per iteration at batch = max_batch:
@@ -158,6 +178,7 @@ typedef struct {
     int time_blocks;                    /* pair-kernel time blocks per warp and unit */
     int apply_mode;                     /* AMTO_APPLY_BATCHED, _FUSED or _KRONECKER */
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
+    int multipliers;                    /* AMTO_MULT_PAIRS or AMTO_MULT_AGGREGATE */
 } amto_info;
 
 /*
@@ -255,6 +276,7 @@ amto_status amto_solve_static(amto_plan plan, const float* start, const float* g
  * All outputs are device pointers, each may be NULL:
  *   lambda_out [batch][3][p][m], alpha_out/beta_out/d_out [batch][p][m],
  * float32.  `batch` must equal the last solve's batch.  Asynchronous.
+ * EINVAL if lambda_out is given for an AMTO_MULT_AGGREGATE plan.
  */
 amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out,
                            float* alpha_out, float* beta_out, float* d_out,

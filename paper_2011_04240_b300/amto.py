@@ -22,6 +22,7 @@ PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
 PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
 APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED, APPLY_KRONECKER = range(4)
 LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
+MULT_AUTO, MULT_PAIRS, MULT_AGGREGATE = range(3)
 MIXED_FUSED, MIXED_BRANCHES = range(2)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
@@ -44,7 +45,7 @@ class Params(ctypes.Structure):
                 ("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
-                ("rho_stage_iters", ctypes.c_int)]
+                ("rho_stage_iters", ctypes.c_int), ("multipliers", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -54,7 +55,8 @@ class Info(ctypes.Structure):
                 ("lambda_floats", ctypes.c_longlong), ("kkt_check", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
                 ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
-                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int)]
+                ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
+                ("multipliers", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -252,13 +254,14 @@ class Planner:
                  proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
                  apply_mode: int = 0, loop_mode: int = 0, rho_stages: int = 0,
-                 rho_growth: float = 1.0, rho_stage_iters: int = 1):
+                 rho_growth: float = 1.0, rho_stage_iters: int = 1, multipliers: int = 0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
-                             apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters)
+                             apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters,
+                             multipliers)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)
@@ -315,10 +318,13 @@ class Planner:
         return xi, resid, iters
 
     def state(self, stream=None):
-        """(lambda [B,3,p,m], alpha, beta, d [B,p,m]) of the last solve."""
+        """(lambda [B,3,p,m], alpha, beta, d [B,p,m]) of the last solve; lambda
+        is None for a plan that keeps the multipliers aggregated."""
         torch = self._torch
         B = self.last_batch
-        lam = torch.empty((B, 3, self.p, self.m), device=self.device, dtype=torch.float32)
+        lam = None
+        if self.info.multipliers != MULT_AGGREGATE:
+            lam = torch.empty((B, 3, self.p, self.m), device=self.device, dtype=torch.float32)
         al = torch.empty((B, self.p, self.m), device=self.device, dtype=torch.float32)
         be = torch.empty_like(al)
         d = torch.empty_like(al)

@@ -165,7 +165,8 @@ struct amto_plan_s {
     // state for max_batch instances (device)
     float* xi = nullptr;       // [B][3][n nv]
     float* beq = nullptr;      // [B][3][n nb]
-    float* lam[2] = {nullptr, nullptr};  // [B][lam_floats]
+    float* lam[2] = {nullptr, nullptr};  // [B][lam_floats] (PAIRS form only)
+    float* Lagg = nullptr;     // [B][3][n nv] A_fc^T lambda (AGGREGATE form only)
     float* gpart = nullptr;    // [B][n_chunks][3][n nv]
     float* rpart = nullptr;    // [B][n_chunks]
     float* rhs = nullptr;      // [B][3][kp] (TF32-rounded in tensor-core modes)
@@ -186,6 +187,7 @@ struct amto_plan_s {
     bool fused = false;        // K^-1 applied per instance inside the pair kernel
     bool block = false;        // the loop runs in the one-block-per-instance solver
     bool kron = false;         // K^-1 applied in its exact agent-structured form
+    bool agg = false;          // multipliers kept as A_fc^T lambda (AMTO_MULT_AGGREGATE)
     cudaStream_t cap_stream = nullptr;
     std::map<int, amto::Graph> graphs;
 
@@ -241,6 +243,13 @@ size_t block_solver_smem(const PairGeom& g, int n, int m, int nv, int nb);
 amto_status configure_block_solver(amto_plan_s* pl);
 // Whether a plan with these parameters runs its loop in the block solver.
 bool loop_block(const amto_params& p);
+// AMTO_MULT_AUTO resolved: the aggregated multipliers where the reading and
+// the loop allow them.
+bool mult_aggregate(const amto_params& p);
+// L = A_fc^T lambda_init of a warm start (AGGREGATE plans), one block per
+// instance and axis.
+amto_status launch_lambda_aggregate(amto_plan_s* pl, int batch, const float* lambda_init,
+                                    cudaStream_t s);
 amto_status launch_block_solver(amto_plan_s* const* pls, const int* batch, int ng, cudaStream_t s);
 cudaError_t raise_smem_cap(const void* fn, size_t bytes);
 // Tile grid, split-K count and K per split of the tensor-core apply.

@@ -54,7 +54,7 @@ void free_plan(amto_plan_s* pl) {
     }
     pl->graphs.clear();
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kag, pl->Kinv64, pl->Ktop,
-                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->gpart, pl->rpart, pl->rhs,
+                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
                     pl->gemm_tk, pl->ctl};
@@ -193,6 +193,16 @@ amto_status validate_params(const amto_params& p) {
     if (p.loop_mode == AMTO_LOOP_BLOCK && p.apply_mode != AMTO_APPLY_KRONECKER &&
         (p.precision != AMTO_PREC_FP32 || p.apply_mode == AMTO_APPLY_FUSED))
         return einval("the block solver applies K^-1 in float32 (dense or structured) only");
+    if (p.multipliers < AMTO_MULT_AUTO || p.multipliers > AMTO_MULT_AGGREGATE)
+        return einval("multipliers must be one of AMTO_MULT_*");
+    if (p.multipliers == AMTO_MULT_AGGREGATE) {
+        if (p.proj_mode != AMTO_PROJ_NOLAMBDA)
+            return einval("aggregated multipliers need AMTO_PROJ_NOLAMBDA (the literal reading "
+                          "uses lambda per pair in the d step)");
+        if (apply_fused(p) || loop_block(p))
+            return einval("aggregated multipliers need the graph loop and the batched or "
+                          "Kronecker apply");
+    }
     if (p.tile_group != 0 && p.tile_group != 8 && p.tile_group != 16 && p.tile_group != 32)
         return einval("tile_group must be 0 (automatic), 8, 16 or 32");
     if (p.tile_time_blocks < 0 || p.tile_time_blocks > 8)
@@ -266,6 +276,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     pl->kron = p.apply_mode == AMTO_APPLY_KRONECKER;
     pl->block = loop_block(p);
+    pl->agg = mult_aggregate(p);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
     pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
     const bool tc = prec_tc(p.precision), bf = prec_bf16(p.precision);
@@ -306,8 +317,12 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     ALLOC(pl->xi, (size_t)B * 3 * nvn);
     ALLOC(pl->beq, (size_t)B * 3 * n * nb);
-    ALLOC(pl->lam[0], (size_t)B * pl->geo.lam_floats);
-    ALLOC(pl->lam[1], (size_t)B * pl->geo.lam_floats);
+    if (pl->agg) {
+        ALLOC(pl->Lagg, (size_t)B * 3 * nvn);
+    } else {
+        ALLOC(pl->lam[0], (size_t)B * pl->geo.lam_floats);
+        ALLOC(pl->lam[1], (size_t)B * pl->geo.lam_floats);
+    }
     ALLOC(pl->gpart, (size_t)B * pl->geo.n_chunks * 3 * nvn);
     ALLOC(pl->rpart, (size_t)B * pl->geo.n_chunks);
     ALLOC(pl->rhs, (size_t)B * 3 * pl->kp);
@@ -380,6 +395,8 @@ amto_status amto_solve(amto_plan plan, int batch, const float* start, const floa
     cudaStream_t s = (cudaStream_t)stream;
     amto_status st = launch_setup(plan, batch, start, goal, bc_extra, xi_init, max_iters, tol, s);
     if (st != AMTO_OK) return st;
+    if (plan->agg && lambda_init) st = launch_lambda_aggregate(plan, batch, lambda_init, s);
+    if (st != AMTO_OK) return st;
     st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, 0, 0, s);
     if (st != AMTO_OK) return st;
     if (plan->block) {
@@ -413,6 +430,9 @@ amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out, float* 
     if (!plan) return einval("plan is NULL");
     if (batch < 1 || batch != plan->last_batch)
         return einval("batch must equal the last solve's batch");
+    if (lambda_out && plan->agg)
+        return einval("this plan keeps the multipliers aggregated (A_fc^T lambda, "
+                      "AMTO_MULT_AGGREGATE); create it with AMTO_MULT_PAIRS to read them");
     DeviceGuard g(plan->device);
     return launch_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, (cudaStream_t)stream);
 }
@@ -428,7 +448,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->group = plan->geo.G;
     out->t_chunk = plan->geo.TC;
     out->n_chunks = plan->geo.n_chunks;
-    out->lambda_floats = plan->geo.lam_floats;
+    out->lambda_floats = plan->agg ? 0 : plan->geo.lam_floats;
     out->kkt_check = plan->kkt_check;
     out->device_bytes = plan->bytes;
     out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
@@ -437,6 +457,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->apply_mode = plan->kron ? AMTO_APPLY_KRONECKER
                     : plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
     out->loop_mode = plan->block ? AMTO_LOOP_BLOCK : AMTO_LOOP_GRAPH;
+    out->multipliers = plan->agg ? AMTO_MULT_AGGREGATE : AMTO_MULT_PAIRS;
     if (plan->block) {
         out->launches_per_iteration = 0;
         out->launches_fixed = 5;  // setup, initial projection, block solver, residual, outputs

@@ -37,7 +37,7 @@ namespace amto {
 
 // Device bytes of one resident instance of a plan (the state amto_create
 // allocates per unit of max_batch).
-size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision) {
+size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision, int proj_mode) {
     // the larger multiplier layout of the two automatic lane-group choices
     const PairGeom g1 = choose_geometry(n, m, 0, 0, 1), g2 = choose_geometry(n, m, 0, 0, 1 << 20);
     const PairGeom g = g1.lam_floats >= g2.lam_floats ? g1 : g2;
@@ -46,7 +46,11 @@ size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision)
     size_t b = 0;
     b += 4 * 3 * nvn;                          // xi
     b += 4 * 3 * (size_t)n * nb;               // b_eq
-    b += 2 * 4 * (size_t)g.lam_floats;         // multipliers (two buffers)
+    // multipliers: two per-pair buffers, or A_fc^T lambda where the plan
+    // aggregates them (lambda-free reading; the block solver, possible for
+    // float32 plans of <= 8 agents, keeps the per-pair form)
+    const bool agg = proj_mode == AMTO_PROJ_NOLAMBDA && !(precision == AMTO_PREC_FP32 && n <= 8);
+    b += agg ? 4 * 3 * nvn : 2 * 4 * (size_t)g.lam_floats;
     b += 4 * (size_t)g.n_chunks * 3 * nvn;     // unit partials
     b += 4 * (size_t)g.n_chunks;
     const size_t kp8 = (kdim + 7) / 8 * 8;
@@ -431,7 +435,8 @@ amto_status amto_server_create(const amto_server_params* prm, amto_server* out) 
     sv->inbox.resize(p.n_sizes);
     for (int i = 0; i < p.n_sizes && st == AMTO_OK; ++i) {
         const int n = p.sizes[i];
-        const size_t per = instance_bytes(n, p.m_steps, p.poly_degree, AMTO_BC_ALL, p.precision);
+        const size_t per = instance_bytes(n, p.m_steps, p.poly_degree, AMTO_BC_ALL, p.precision,
+                                          p.proj_mode);
         long long slots = (long long)(share / per);
         if (slots > p.max_slots) slots = p.max_slots;
         if (slots < 1) {

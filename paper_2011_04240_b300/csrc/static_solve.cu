@@ -95,8 +95,10 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     };
     const size_t o_xi = take(sizeof(float) * 3 * nvn);
     const size_t o_beq = take(sizeof(float) * 3 * pl.n * pl.nb);
-    const size_t o_lam0 = take(sizeof(float) * (size_t)pl.geo.lam_floats);
-    const size_t o_lam1 = take(sizeof(float) * (size_t)pl.geo.lam_floats);
+    const size_t lam_b = pl.agg ? 0 : sizeof(float) * (size_t)pl.geo.lam_floats;
+    const size_t o_lam0 = take(lam_b);
+    const size_t o_lam1 = take(lam_b);
+    const size_t o_lagg = take(pl.agg ? sizeof(float) * 3 * nvn : 0);
     const size_t o_gpart = take(sizeof(float) * NC * 3 * nvn);
     const size_t o_rpart = take(sizeof(float) * NC);
     const size_t o_rhs = take(sizeof(float) * 3 * (size_t)pl.kp);
@@ -145,8 +147,10 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     v.ks_top = pl.ks_top; v.ks_ag = pl.ks_ag;
     v.xi = reinterpret_cast<float*>(base + o_xi);
     v.beq = reinterpret_cast<float*>(base + o_beq);
-    v.lam[0] = reinterpret_cast<float*>(base + o_lam0);
-    v.lam[1] = reinterpret_cast<float*>(base + o_lam1);
+    v.agg = pl.agg;
+    v.lam[0] = pl.agg ? nullptr : reinterpret_cast<float*>(base + o_lam0);
+    v.lam[1] = pl.agg ? nullptr : reinterpret_cast<float*>(base + o_lam1);
+    v.Lagg = pl.agg ? reinterpret_cast<float*>(base + o_lagg) : nullptr;
     v.gpart = reinterpret_cast<float*>(base + o_gpart);
     v.rpart = reinterpret_cast<float*>(base + o_rpart);
     v.rhs = reinterpret_cast<float*>(base + o_rhs);

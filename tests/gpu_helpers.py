@@ -21,13 +21,17 @@ def rel_inf(a, b) -> float:
 PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4}
 
 
+MULT = {"auto": 0, "pairs": 1, "aggregate": 2}
+
+
 def planner(prob: W.Problem, mode="R2", max_batch=1, bc_mask=63, precision="fp32",
-            tile_group=0, tile_time_blocks=0, loop_mode=0):
+            tile_group=0, tile_time_blocks=0, loop_mode=0, multipliers="auto"):
     from paper_2011_04240_b300 import Planner
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree,
                    bc_mask=bc_mask, proj_mode=MODES[mode], max_batch=max_batch,
                    precision=PRECISIONS[precision], tile_group=tile_group,
-                   tile_time_blocks=tile_time_blocks, loop_mode=loop_mode)
+                   tile_time_blocks=tile_time_blocks, loop_mode=loop_mode,
+                   multipliers=MULT[multipliers])
 
 
 def to_dev(x, dev):
@@ -53,7 +57,8 @@ def gpu_state(pl):
     import torch
     lam, al, be, d = pl.state()
     torch.cuda.synchronize()
-    return lam.cpu().numpy(), al.cpu().numpy(), be.cpu().numpy(), d.cpu().numpy()
+    lam = None if lam is None else lam.cpu().numpy()  # None: aggregated multipliers
+    return lam, al.cpu().numpy(), be.cpu().numpy(), d.cpu().numpy()
 
 
 def oracle_mats(prob: W.Problem, bc_mask=63):

@@ -107,7 +107,7 @@ def test_one_iteration_from_warm_state(n, m, mode, G, QW):
     p = n * (n - 1) // 2
     ws = O.warm_state(M, xi0.astype(np.float64), lam0.astype(np.float64), mode)
     ref = O.am_iteration(M, ws, O.boundary_values(prob.start, prob.goal), mode)
-    pl = planner(prob, mode, tile_group=G, tile_time_blocks=QW)
+    pl = planner(prob, mode, tile_group=G, tile_time_blocks=QW, multipliers="pairs")
     xi, r, k = gpu_solve(pl, [prob], 1, xi_init=xi0.reshape(1, 3, n, -1),
                          lambda_init=lam0.reshape(1, 3, p, m))
     assert k[0] == 1
@@ -211,7 +211,7 @@ def test_fp64_final_residual_is_the_maximum(n, mode, k, B):
         probs = W.config4(B)
     else:
         probs = [W.random_box(n, 900 + i, box=(8.0, 8.0, 4.0)) for i in range(B)]
-    pl = planner(probs[0], mode, max_batch=B)
+    pl = planner(probs[0], mode, max_batch=B, multipliers="pairs")
     gpu_solve(pl, probs, k - 1)
     lam_a = gpu_state(pl)[0].astype(np.float64)
     x, r, kk = gpu_solve(pl, probs, k)

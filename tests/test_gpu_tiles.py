@@ -20,12 +20,12 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def _planner(prob, B, G=0, QW=0, mode=0, apply_mode=0, precision=0, loop_mode=1):
+def _planner(prob, B, G=0, QW=0, mode=0, apply_mode=0, precision=0, loop_mode=1, multipliers=0):
     """Graph-loop plans (the tiles and apply modes under test are its)."""
     from paper_2011_04240_b300 import Planner
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree, proj_mode=mode,
                    max_batch=B, tile_group=G, tile_time_blocks=QW, apply_mode=apply_mode,
-                   precision=precision, loop_mode=loop_mode)
+                   precision=precision, loop_mode=loop_mode, multipliers=multipliers)
 
 
 @pytest.mark.parametrize("n,m,G,QW", [(16, 100, 8, 1), (16, 100, 8, 4), (16, 100, 16, 2),
@@ -76,7 +76,9 @@ def test_fused_apply_equals_matrix_vector_kernel(n, B, literal):
     from paper_2011_04240_b300 import amto
     probs = [W.random_box(n, 6100 + 5 * n + i, box=(8.0, 8.0, 4.0)) for i in range(B)]
     pf = _planner(probs[0], B, mode=literal, apply_mode=amto.APPLY_FUSED)
-    pb = _planner(probs[0], B, mode=literal, apply_mode=amto.APPLY_BATCHED)
+    # the fused apply keeps the multipliers per pair: compare with the same form
+    pb = _planner(probs[0], B, mode=literal, apply_mode=amto.APPLY_BATCHED,
+                  multipliers=amto.MULT_PAIRS)
     assert pf.info.apply_mode == amto.APPLY_FUSED and pf.info.launches_per_iteration == 1
     assert pb.info.apply_mode == amto.APPLY_BATCHED
     xf, rf, kf = gpu_solve(pf, probs, 300, tol=1e-2)
