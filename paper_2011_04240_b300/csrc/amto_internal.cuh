@@ -123,7 +123,7 @@ struct PairGeom {
 
 // Pair-kernel geometry for n agents and m samples: lane group G and time
 // blocks per warp and unit QW (0: automatic, depending on the batch size).
-PairGeom choose_geometry(int n, int m, int G_req, int QW_req, int max_batch);
+PairGeom choose_geometry(int n, int m, int G_req, int QW_req, int max_batch, bool agg);
 
 struct Graph {
     cudaGraph_t graph = nullptr;

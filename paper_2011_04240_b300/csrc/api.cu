@@ -209,7 +209,7 @@ amto_status validate_params(const amto_params& p) {
         return einval("tile_time_blocks must be in [0, 8]");
     {
         const PairGeom g = choose_geometry(p.n_agents, p.m_steps, p.tile_group, p.tile_time_blocks,
-                                           p.max_batch);
+                                           p.max_batch, mult_aggregate(p));
         if (pair_smem_bytes_host(p.n_agents, p.poly_degree + 1, __builtin_popcount(p.bc_mask),
                                  g.TC, g.npad, apply_fused(p)) > 227 * 1024)
             return einval("the pair-kernel tile does not fit in shared memory; use fewer "
@@ -260,7 +260,8 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->nb = nb;
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
-    pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch);
+    pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch,
+                              mult_aggregate(p));
     pl->fused = apply_fused(p);
     {
         RhoSched& sc = pl->sched;

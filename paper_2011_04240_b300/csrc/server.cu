@@ -39,7 +39,8 @@ namespace amto {
 // allocates per unit of max_batch).
 size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision, int proj_mode) {
     // the larger multiplier layout of the two automatic lane-group choices
-    const PairGeom g1 = choose_geometry(n, m, 0, 0, 1), g2 = choose_geometry(n, m, 0, 0, 1 << 20);
+    const PairGeom g1 = choose_geometry(n, m, 0, 0, 1, false);
+    const PairGeom g2 = choose_geometry(n, m, 0, 0, 1 << 20, false);
     const PairGeom g = g1.lam_floats >= g2.lam_floats ? g1 : g2;
     const int nv = degree + 1, nb = __builtin_popcount(bc_mask);
     const size_t kdim = (size_t)n * (nv + nb), kp = (kdim + 3) / 4 * 4, nvn = (size_t)n * nv;

@@ -125,7 +125,7 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
             p.loop_mode = loops[mi];
             p.max_batch = batch;
             if (loops[mi] == AMTO_LOOP_BLOCK && qws[qi] > 1) continue;  // no time blocks per warp
-            const PairGeom g = choose_geometry(n, p.m_steps, G, qws[qi], batch);
+            const PairGeom g = choose_geometry(n, p.m_steps, G, qws[qi], batch, false);
             if (qws[qi] > 1 && g.TC / 2 >= p.m_steps) continue;  // one unit covers the horizon
             if (validate_params(p) != AMTO_OK) {
                 clear_error();
