@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--precision", default="tf32x3",
                     choices=["fp32", "tf32x3", "bf16x3", "tf32", "bf16"],
                     help="arithmetic of the cached-inverse apply (pair step is float32)")
+    ap.add_argument("--multipliers", default="auto", choices=["auto", "pairs", "aggregate"],
+                    help="multiplier form of the plan (auto: aggregated for this reading)")
     ap.add_argument("--trace", action="store_true",
                     help="run the timed solve from the host loop (no graph), as profilers need")
     ap.add_argument("--no-extras", action="store_true",
@@ -154,10 +156,38 @@ def workload(args, rank):
 
 
 def algorithmic_pair_bytes(n, m, batch):
-    """Bytes the pair step must move per launch: lambda read + write (24 B per
-    pair-time) and the trajectories read (12 B per coefficient row)."""
+    """Bytes the pair step with per-pair multipliers must move per launch:
+    lambda read + write (24 B per pair-time) and the trajectories read (12 B
+    per coefficient row)."""
     pt = m * n * (n - 1) // 2
     return batch * (24 * pt + 3 * 11 * n * 4)
+
+
+# FP32-pipe operations of the lambda-free pair step per pair and sample (one
+# op = one FP32 instruction lane; an FMA counts once): Delta 3, spheroid norm
+# s^2 5, guard max(s^2, FLT_MIN) 1, k = min(0, 1 - 1/s) 2, f_c = Delta k 3,
+# |f_c|^2 3, running max 1, -f_c / +f_c into both agents' sums 6 (1/s itself
+# on the special-function unit, not counted).
+PAIR_OPS = 24
+
+
+def working_set_mb(pl, B):
+    """Bytes one iteration reads or writes in the plan's buffers (MB)."""
+    i = pl.info
+    nvn, kp = i.n_agents * i.nv, (i.kkt_dim + 3) // 4 * 4
+    per = 4 * 3 * nvn * (2 + i.n_chunks) + 2 * 4 * 3 * kp + 2 * 4 * i.lambda_floats
+    return (B * per + 2 * 4 * nvn * kp + 8 * 4 * 3 * B * nvn) / 1e6
+
+
+def alu_peak_tops(sm_count):
+    """FP32-pipe peak in T ops/s: 128 lanes per SM per clock at the measured
+    maximum SM clock."""
+    mhz = 2032.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return sm_count * 128 * mhz * 1e6 / 1e12
 
 
 def source_hash():
@@ -177,15 +207,16 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic(n, batch):
-    """Per-launch DRAM traffic of the pair kernel from the committed ncu summary,
-    scaled to `batch` instances; None if the kernel changed since the capture."""
+def profile_traffic(n, batch, form):
+    """Per-launch DRAM traffic of the pair kernel (`form` "aggregate" or
+    "pairs") from the committed ncu summary, scaled to `batch` instances; None
+    if the kernel changed since the capture."""
     path = os.path.join(ROOT, "profiles", "pair_kernel_shell64.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     mh = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    mb = re.search(r"dram_bytes_per_instance_launch:\s*([0-9.eE+]+)", text)
+    mb = re.search(r"dram_bytes_per_instance_launch_" + form + r":\s*([0-9.eE+]+)", text)
     mn = re.search(r"agents:\s*(\d+)", text)
     if not (mh and mb and mn) or mh.group(1) != source_hash() or int(mn.group(1)) != n:
         return None
@@ -613,8 +644,10 @@ def main():
     probs = workload(args, rank)
     n, m, B, K = probs[0].n, probs[0].m, len(probs), args.steps
     prec = PRECISIONS[args.precision]
+    mult = {"auto": amto.MULT_AUTO, "pairs": amto.MULT_PAIRS,
+            "aggregate": amto.MULT_AGGREGATE}[args.multipliers]
     pl = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
-                 proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
+                 proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B, multipliers=mult)
     s_np, g_np = W.stack(probs)
     s = torch.from_numpy(s_np).cuda()
     g = torch.from_numpy(g_np).cuda()
@@ -623,6 +656,7 @@ def main():
     # warm-up: W iterations (also instantiates the solve graph)
     pl.solve(s, g, max(args.warmup, 3), out=out)
     torch.cuda.synchronize()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB, twice L2
 
     def barrier():
         if world > 1:
@@ -633,6 +667,7 @@ def main():
         pl.set_trace(True)
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
     with ClockSampler(local) as clk:
+        flush.fill_(1.0)  # the timed solve starts with nothing of its state in L2
         barrier()
         torch.cuda.synchronize()
         e0.record(stream)
@@ -654,6 +689,7 @@ def main():
         hx = torch.empty((B, 3, n, 11)).pin_memory()
         hr = torch.empty((B,)).pin_memory()
         hk = torch.empty((B,), dtype=torch.int32).pin_memory()
+        flush.fill_(2.0)
         torch.cuda.synchronize()
         barrier()
         f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -672,25 +708,65 @@ def main():
         extras["e2e"] = {"value": job_throughput(B * K, world, e2e_max), "unit": UNIT,
                          "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                          "note": "one solve of K iterations per timed call; bytes per solve / K"}
-        # per-kernel device time from an event-traced pass of the same solve
-        pl.set_trace(True)
-        pl.solve(s, g, K, out=out)
-        torch.cuda.synchronize()
-        kms, kcnt = pl.stats()
-        pl.set_trace(False)
-        pair_ms = kms[0] / max(kcnt[0], 1)
+        # per-kernel device time from event-traced passes of the same solve:
+        # as in the graph loop (mode 1), and with L2 flushed before every
+        # iteration (mode 2)
+        def traced(mode, plan, iters):
+            plan.set_trace(mode)
+            plan.solve(s, g, iters, out=out)
+            torch.cuda.synchronize()
+            kms, kcnt = plan.stats()
+            plan.set_trace(0)
+            return [kms[k] / max(kcnt[k], 1) for k in range(3)]  # pair, rhs, apply (ms)
+        k_warm = traced(1, pl, K)
+        k_cold = traced(2, pl, min(K, 50))
+        pair_ms = k_warm[0]
         hbm, src = peaks()
-        alg = algorithmic_pair_bytes(n, m, B)
-        achieved = alg / (pair_ms / 1e3) / 1e9
-        extras["roofline"] = {"bound": "hbm", "kernel": "k_pair (fused pair step)",
-                              "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                              "frac": achieved / hbm, "peak_source": src,
-                              "traffic": profile_traffic(n, B),
-                              "algorithmic_bytes_per_launch": alg,
-                              "avg_launch_ms": pair_ms,
-                              "kernel_ms_per_iteration": {"pair": pair_ms,
-                                                          "rhs": kms[1] / max(kcnt[1], 1),
-                                                          "apply": kms[2] / max(kcnt[2], 1)}}
+        pt = B * m * n * (n - 1) // 2
+        agg = pl.info.multipliers == amto.MULT_AGGREGATE
+        if agg:
+            peak = alu_peak_tops(torch.cuda.get_device_properties(local).multi_processor_count)
+            achieved = PAIR_OPS * pt / (pair_ms / 1e3) / 1e12
+            extras["roofline"] = {
+                "bound": "alu", "kernel": "k_pair (pair step, aggregated multipliers)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "derived: 128 FP32 lanes/SM/clock x SMs x measured max SM clock; "
+                               "one FP32 instruction lane = 1 op (FMA counted once)",
+                "traffic": profile_traffic(n, B, "aggregate"),
+                "algorithmic_ops_per_launch": PAIR_OPS * pt, "ops_per_pair_time": PAIR_OPS,
+                "avg_launch_ms": pair_ms}
+        else:
+            alg = algorithmic_pair_bytes(n, m, B)
+            achieved = alg / (pair_ms / 1e3) / 1e9
+            extras["roofline"] = {"bound": "hbm", "kernel": "k_pair (pair step, per-pair multipliers)",
+                                  "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                  "frac": achieved / hbm, "peak_source": src,
+                                  "traffic": profile_traffic(n, B, "pairs"),
+                                  "algorithmic_bytes_per_launch": alg, "avg_launch_ms": pair_ms}
+        extras["roofline"]["kernel_ms_per_iteration"] = {
+            "pair": k_warm[0], "rhs": k_warm[1], "apply": k_warm[2]}
+        extras["cold_l2"] = {
+            "note": "event-traced iterations with L2 flushed (256 MiB write) before each one",
+            "kernel_ms_per_iteration": {"pair": k_cold[0], "rhs": k_cold[1], "apply": k_cold[2]},
+            "value": job_throughput(B, world, max_over_ranks(sum(k_cold), world, "cuda")),
+            "unit": UNIT}
+        if agg:
+            # the same workload with the multipliers kept per pair (Algorithm 1's
+            # own state): its pair step is bound by HBM traffic
+            pp = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
+                         proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B,
+                         multipliers=amto.MULT_PAIRS)
+            pp.solve(s, g, 3, out=out)
+            kp = traced(1, pp, 20)
+            alg = algorithmic_pair_bytes(n, m, B)
+            ach = alg / (kp[0] / 1e3) / 1e9
+            extras["roofline_pairs_form"] = {
+                "bound": "hbm", "kernel": "k_pair (pair step, per-pair multipliers)",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_source": src, "traffic": profile_traffic(n, B, "pairs"),
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kp[0],
+                "kernel_ms_per_iteration": {"pair": kp[0], "rhs": kp[1], "apply": kp[2]}}
+            pp.close()
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
             extras["rho_schedule_per_instance"] = plain_per_instance(
@@ -708,8 +784,14 @@ def main():
                                        "lambda-free projection, fixed iterations",
                            "batch_per_gpu": B, "agents": n, "m": m,
                            "apply_precision": args.precision,
-                           "l2": "inputs larger than L2 (multiplier state "
-                                 f"{2 * pl.info.lambda_floats * 4 * B / 1e9:.2f} GB)",
+                           "multipliers": "aggregated (A_fc^T lambda)"
+                                          if pl.info.multipliers == amto.MULT_AGGREGATE
+                                          else "per pair",
+                           "l2": "L2 flushed (256 MiB write) before the timed solve; "
+                                 f"per-iteration state {working_set_mb(pl, B):.0f} MB "
+                                 "(trajectories, unit partials, multipliers, right-hand "
+                                 "sides, K^-1) stays in L2 across the solve's iterations "
+                                 "when it fits; see cold_l2 for every iteration from HBM",
                            "parallelism": f"replicas x{world}"},
                 "clocks": clk.summary(),
                 # setup, initial projection, K x (rhs, apply [+ split-K reduce], pair),

@@ -303,8 +303,11 @@ amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count);
 /*
  * amto_set_trace - 1: later solves launch each kernel from a host loop and
  * bracket it with CUDA events on the solve's stream (per-kernel timing, no
- * graph, one host synchronisation per iteration); 0: graph mode (default).
- * Results are identical in both modes.
+ * graph, one host synchronisation per iteration); 2: as 1, and before each
+ * iteration the L2 cache is flushed by writing a 256 MiB device buffer (taken
+ * by this call, freed with the plan), outside the timed events, so every
+ * iteration's kernels start from HBM; 0: graph mode (default).  Results are
+ * identical in all modes.  ENOMEM if the flush buffer cannot be allocated.
  */
 amto_status amto_set_trace(amto_plan plan, int on);
 

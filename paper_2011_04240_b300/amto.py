@@ -214,8 +214,10 @@ def get_stats(plan):
     return list(ms), list(cnt)
 
 
-def set_trace(plan, on: bool) -> None:
-    _check(load().amto_set_trace(plan, 1 if on else 0))
+def set_trace(plan, on) -> None:
+    """0/False: graph loop; 1/True: traced loop; 2: traced, L2 flushed before
+    every iteration."""
+    _check(load().amto_set_trace(plan, int(on)))
 
 
 def tune(params: Params, batch: int, iters: int = 20) -> dict:
@@ -338,7 +340,7 @@ class Planner:
         get_kkt_inverse(self.plan, out.ctypes.data)
         return out
 
-    def set_trace(self, on: bool):
+    def set_trace(self, on):
         set_trace(self.plan, on)
 
     def stats(self):

@@ -192,7 +192,8 @@ struct amto_plan_s {
     std::map<int, amto::Graph> graphs;
 
     // tracing
-    int trace = 0;
+    int trace = 0;               // 0 graph loop, 1 traced loop, 2 traced with L2 flushes
+    float4* l2_flush = nullptr;  // 256 MiB written before each iteration in trace mode 2
     double stat_ms[amto::KSTAT_N] = {0, 0, 0};
     int stat_cnt[amto::KSTAT_N] = {0, 0, 0};
 };

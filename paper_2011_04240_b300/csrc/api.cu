@@ -57,7 +57,7 @@ void free_plan(amto_plan_s* pl) {
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
-                    pl->gemm_tk, pl->ctl};
+                    pl->gemm_tk, pl->ctl, pl->l2_flush};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (pl->ctl_host) cudaFreeHost(pl->ctl_host);
@@ -114,6 +114,14 @@ amto_status build_graph(amto_plan_s* pl, int batch, Graph& out) {
     return AMTO_OK;
 }
 
+constexpr size_t kFlushBytes = (size_t)256 << 20;  // twice the L2 cache
+
+__global__ void k_flush_l2(float4* buf, size_t n, float v) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        buf[i] = make_float4(v, v, v, v);
+}
+
 // Host-driven loop with CUDA events around every launch (amto_set_trace).
 // The loop runs while the last pair pass left an instance flagged to
 // iterate, at most max_iters + 1 passes (the same bound as the graph loop).
@@ -129,6 +137,14 @@ amto_status run_traced(amto_plan_s* pl, int batch, int max_iters, cudaStream_t s
             break;
         }
         if (pl->ctl_host->active_last == 0) break;
+        if (pl->trace == 2 && pl->l2_flush) {  // every kernel of the iteration starts cold
+            k_flush_l2<<<4 * pl->num_sms, 512, 0, s>>>(pl->l2_flush, kFlushBytes / 16, (float)it);
+            if (cudaGetLastError() != cudaSuccess) {
+                set_error("traced solve: L2 flush launch failed");
+                st = AMTO_ECUDA;
+                break;
+            }
+        }
         cudaEventRecord(ev[0], s);
         st = launch_rhs(pl, batch, s);
         cudaEventRecord(ev[1], s);
@@ -488,7 +504,17 @@ amto_status amto_get_stats(amto_plan plan, double* out_ms, int* out_count) {
 amto_status amto_set_trace(amto_plan plan, int on) {
     clear_error();
     if (!plan) return einval("plan is NULL");
-    plan->trace = on ? 1 : 0;
+    if (on < 0 || on > 2) return einval("trace mode must be 0, 1 or 2");
+    if (on == 2 && !plan->l2_flush) {
+        DeviceGuard g(plan->device);
+        if (cudaMalloc((void**)&plan->l2_flush, kFlushBytes) != cudaSuccess) {
+            cudaGetLastError();
+            plan->l2_flush = nullptr;
+            set_error("cudaMalloc of the L2 flush buffer failed");
+            return AMTO_ENOMEM;
+        }
+    }
+    plan->trace = on;
     return AMTO_OK;
 }
 
