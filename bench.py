@@ -329,8 +329,8 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4), rho_schedule=None):
     import torch
     import workloads as W
     from paper_2011_04240_b300 import Planner
-    J, g, E = rho_schedule if rho_schedule else (0, 1.0, 1)
-    pl = Planner(16, 100, 8.0, max_batch=1, rho_stages=J, rho_growth=g, rho_stage_iters=E)
+    J, gr, E = rho_schedule if rho_schedule else (0, 1.0, 1)
+    pl = Planner(16, 100, 8.0, max_batch=1, rho_stages=J, rho_growth=gr, rho_stage_iters=E)
     lat, its, res = [], [], []
     for rep in range(2):
         for sd in seeds:
@@ -351,7 +351,7 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4), rho_schedule=None):
     lat = np.array(lat)
     wl = "16 agents, 6x6x3 m box, m=100, tol 1e-2 / 500 iterations, batch 1"
     if rho_schedule:
-        wl += f", rho = {g:.4g}^j for j < {J}, {E} solves per stage"
+        wl += f", rho = {gr:.4g}^j for j < {J}, {E} solves per stage"
     return {"workload": wl,
             "value": float(sum(its) / (lat.sum() / 1e3)), "unit": UNIT,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
