@@ -57,6 +57,17 @@ Readings of ambiguous passages (each also listed in the design notes):
             stage min(J-1, (k-1) div E); iteration k runs entirely with rho_k
             (the target b of Eq. b_f, the d step and the lambda update), and
             lambda carries over unchanged across a switch.
+  R-obst    Sec. IV-A (static obstacles by their circumscribing spheres; only
+            the cost of A_fc^T b grows with their number, linearly): every
+            (agent i, obstacle o, sample t) is one more row of A_fc with +P in
+            agent i's columns and a fixed partner, the obstacle centre c_o.
+            Delta = x_i(t) - c_o is projected on the combined agent-obstacle
+            spheroid whose semi-axes (a_o, b_o) are given per obstacle; the
+            row's target is c_o + d u - lambda/rho and its lambda is updated
+            like a pair's (same reading R-lambda).  rho A_fc^T A_fc gains
+            n_obs rho P^T P per agent, so the cached inverse depends on
+            (n, n_obs, rho).  Obstacle rows are ordered agent-major, then
+            obstacle, then time; lambda^0 = 0 on them; they count in r_max.
 """
 from __future__ import annotations
 
@@ -147,6 +158,8 @@ class Matrices:
     A_fc: sp.csr_matrix    # (p m) x (n nv)
     K: np.ndarray          # KKT matrix of Eq. (kkt_step_x)
     Kinv: np.ndarray       # its inverse (Remark 1: computed once)
+    n_obs: int = 0         # static obstacles per instance (reading R-obst)
+    A_obs: sp.csr_matrix | None = None   # (n n_obs m) x (n nv) agent-obstacle rows
 
     @property
     def nv(self):
@@ -157,24 +170,42 @@ class Matrices:
         return self.A.shape[0]
 
 
+def obstacle_matrix(P, n: int, n_obs: int):
+    """Agent-obstacle rows of A_fc (reading R-obst) as a sparse matrix: block
+    (i, o) occupies rows [(i n_obs + o) m, (i n_obs + o + 1) m) with +P in
+    agent i's columns; the partner (the obstacle centre) is fixed."""
+    m, nv = P.shape
+    blocks = []
+    for i in range(n):
+        for o in range(n_obs):
+            row = [sp.csr_matrix((m, nv)) for _ in range(n)]
+            row[i] = sp.csr_matrix(P)
+            blocks.append(row)
+    if not blocks:
+        return sp.csr_matrix((0, n * nv))
+    return sp.bmat(blocks, format="csr")
+
+
 def build_matrices(n: int, m: int, degree: int, T: float, a: float, b: float,
-                   rho: float, bc_mask: int = BC_ALL) -> Matrices:
+                   rho: float, bc_mask: int = BC_ALL, n_obs: int = 0) -> Matrices:
     """Assemble Q_x, A_eq, A_fc and the KKT matrix, and invert it (Eq. kkt_step_x).
 
     The inverse is a dense LAPACK LU-based inverse (partial pivoting); it is
-    computed once per (n, rho, P) as Remarks 1-2 state.
+    computed once per (n, rho, P) as Remarks 1-2 state (and per obstacle
+    count, reading R-obst).
     """
     P, dP, ddP = bernstein_basis(degree, m, T)
     A = boundary_rows(P, dP, ddP, bc_mask)
     Q = np.kron(np.eye(n), ddP.T @ ddP)
     A_eq = np.kron(np.eye(n), A)
     A_fc = pair_matrix(P, n)
-    H = Q + rho * (A_fc.T @ A_fc).toarray()
+    A_obs = obstacle_matrix(P, n, n_obs)
+    H = Q + rho * (A_fc.T @ A_fc).toarray() + rho * (A_obs.T @ A_obs).toarray()
     nz = A_eq.shape[0]
     K = np.block([[H, A_eq.T], [A_eq, np.zeros((nz, nz))]])
     Kinv = np.linalg.inv(K)
     return Matrices(n, m, degree, T, a, b, rho, bc_mask, P, dP, ddP, A, Q, A_eq,
-                    A_fc, K, Kinv)
+                    A_fc, K, Kinv, n_obs, A_obs)
 
 
 def boundary_values(start, goal, bc_mask: int = BC_ALL, bc_extra=None):
@@ -224,22 +255,29 @@ def d_step(W, U):
     return np.maximum(1.0, d_hat)
 
 
-def projection(D, lam, M: Matrices, mode: str = "R2"):
-    """alpha, beta, d steps for all pair-times (Eqs. sphere_project, step_d)."""
+def projection(D, lam, M: Matrices, mode: str = "R2", a=None, b=None):
+    """alpha, beta, d steps for all pair-times (Eqs. sphere_project, step_d).
+
+    `a`, `b` (scalars or one value per row) replace the agents' semi-axes,
+    for the agent-obstacle rows (reading R-obst)."""
+    a = M.a if a is None else a
+    b = M.b if b is None else b
     if mode == "R1":
         Wab = D + lam / M.rho
     else:
         Wab = D
-    alpha, beta = alpha_beta(Wab, M.a, M.b)
-    U = spheroid_direction(alpha, beta, M.a, M.b)
+    alpha, beta = alpha_beta(Wab, a, b)
+    U = spheroid_direction(alpha, beta, a, b)
     Wd = D if mode == "R3" else D + lam / M.rho
     d = d_step(Wd, U)
     return alpha, beta, d, U
 
 
-def target_vector(alpha, beta, d, lam, M: Matrices):
+def target_vector(alpha, beta, d, lam, M: Matrices, a=None, b=None):
     """b_fc of Eq. (b_f) per axis: l d sin/cos terms minus lambda/rho."""
-    return d * spheroid_direction(alpha, beta, M.a, M.b) - lam / M.rho
+    a = M.a if a is None else a
+    b = M.b if b is None else b
+    return d * spheroid_direction(alpha, beta, a, b) - lam / M.rho
 
 
 def qp_step(M: Matrices, bfc, beq):
@@ -391,3 +429,76 @@ def warm_state(M: Matrices, xi, lam, mode: str = "R2") -> State:
 def positions(M: Matrices, xi):
     """x_i(t_k) = P c_{x_i}: (3, n, m)."""
     return np.einsum("tk,ank->ant", M.P, xi.reshape(3, M.n, M.nv))
+
+
+# ---------------------------------------------------------------------------
+# Static obstacles (reading R-obst)
+# ---------------------------------------------------------------------------
+
+def obstacle_rows(M: Matrices, obstacles):
+    """Per agent-obstacle row (i, o, t): the centre c_o (3, rows) and the
+    semi-axes a_o, b_o (rows,).  obstacles: (n_obs, 5) = (cx, cy, cz, a_o, b_o)."""
+    ob = np.asarray(obstacles, np.float64).reshape(M.n_obs, 5)
+    o_of_row = np.tile(np.repeat(np.arange(M.n_obs), M.m), M.n)
+    return ob[o_of_row, :3].T.copy(), ob[o_of_row, 3].copy(), ob[o_of_row, 4].copy()
+
+
+def obstacle_differences(M: Matrices, xi, C):
+    """Delta = x_i(t) - c_o per axis: (3, n n_obs m)."""
+    return np.stack([M.A_obs @ xi[ax] for ax in range(3)]) - C
+
+
+@dataclasses.dataclass
+class ObstacleState:
+    lam: np.ndarray      # (3, n n_obs m)
+    alpha: np.ndarray
+    beta: np.ndarray
+    d: np.ndarray
+    r_max: float
+
+
+def qp_step_obstacles(M: Matrices, bfc, bobs, beq):
+    """QP of Eq. (kkt_step_x) with the agent-obstacle rows stacked under the
+    pair rows: rhs = [rho (A_fc^T b_fc + A_obs^T b_obs) ; b_eq]."""
+    nvn = M.n * M.nv
+    g = np.stack([M.rho * (M.A_fc.T @ bfc[ax] + M.A_obs.T @ bobs[ax]) for ax in range(3)])
+    rhs = np.concatenate([g, beq], axis=1)
+    return (M.Kinv @ rhs.T).T[:, :nvn]
+
+
+def solve_obstacles(M: Matrices, start, goal, obstacles, max_iters: int, tol: float = 0.0,
+                    mode: str = "R2", Ms: list | None = None, stage_iters: int = 1,
+                    history: list | None = None):
+    """Algorithm 1 with static obstacles (reading R-obst); returns (State of
+    the pairs, ObstacleState).  r_max is over pair and obstacle rows.  `Ms`
+    (optional): matrices of the rho stages (same n_obs), used as in
+    `solve_schedule`."""
+    beq = boundary_values(start, goal, M.bc_mask)
+    C, a_o, b_o = obstacle_rows(M, obstacles)
+    xi = initial_trajectories(M, beq)
+    D = pair_differences(M, xi)
+    lam = np.zeros_like(D)
+    alpha, beta, d, U = projection(D, lam, M, mode)
+    Do = obstacle_differences(M, xi, C)
+    lam_o = np.zeros_like(Do)
+    al_o, be_o, d_o, U_o = projection(Do, lam_o, M, mode, a_o, b_o)
+    r = max(residual_max(D - d * U), residual_max(Do - d_o * U_o))
+    k = 0
+    while k < max_iters:
+        Mk = M if Ms is None else Ms[rho_stage(k + 1, len(Ms), stage_iters)]
+        bfc = target_vector(alpha, beta, d, lam, Mk)
+        bobs = C + target_vector(al_o, be_o, d_o, lam_o, Mk, a_o, b_o)
+        xi = qp_step_obstacles(Mk, bfc, bobs, beq)
+        D = pair_differences(Mk, xi)
+        alpha, beta, d, U = projection(D, lam, Mk, mode)
+        lam, fc = lambda_update(lam, D, d, U, Mk.rho)
+        Do = obstacle_differences(Mk, xi, C)
+        al_o, be_o, d_o, U_o = projection(Do, lam_o, Mk, mode, a_o, b_o)
+        lam_o, fco = lambda_update(lam_o, Do, d_o, U_o, Mk.rho)
+        r = max(residual_max(fc), residual_max(fco))
+        k += 1
+        if history is not None:
+            history.append(r)
+        if r < tol:
+            break
+    return (State(xi, lam, alpha, beta, d, r, k), ObstacleState(lam_o, al_o, be_o, d_o, r))

@@ -14,6 +14,7 @@ import tests.test_oracle_basis as TB
 import tests.test_oracle_convergence as TC
 import tests.test_oracle_kkt as TK
 import tests.test_oracle_projection as TP
+import tests.test_oracle_obstacles as TO
 import tests.test_oracle_qp as TQ
 
 
@@ -62,7 +63,21 @@ def _basis_derivative_sign(degree, m, T):
     return P, -dP, ddP
 
 
-_orig = {k: getattr(OA, k) for k in ["pair_matrix", "alpha_beta", "bernstein_basis"]}
+def _obstacle_difference_sign(M, xi, C):
+    return C - np.stack([M.A_obs @ xi[ax] for ax in range(3)])
+
+
+def _obstacle_axes_swapped(M, obstacles):
+    C, a_o, b_o = _orig["obstacle_rows"](M, obstacles)
+    return C, b_o, a_o
+
+
+def _obstacle_rows_missing_from_gram(P, n, n_obs):
+    return _orig["obstacle_matrix"](P, n, 0)
+
+
+_orig = {k: getattr(OA, k) for k in ["pair_matrix", "alpha_beta", "bernstein_basis",
+                                     "obstacle_rows", "obstacle_matrix"]}
 
 MUTATIONS = {
     "pair signs swapped": ("pair_matrix", _pair_matrix_signs_swapped,
@@ -82,6 +97,12 @@ MUTATIONS = {
                              [(TQ.test_qp_step_kkt_optimality_and_boundary_exactness,)]),
     "derivative sign": ("bernstein_basis", _basis_derivative_sign,
                         [(TB.test_derivatives_match_symbolic_differentiation, 10, 50, 5.0)]),
+    "obstacle difference sign": ("obstacle_differences", _obstacle_difference_sign,
+                                 [(TO.test_solutions_clear_the_obstacle, "R3")]),
+    "obstacle l_xy and l_z swapped": ("obstacle_rows", _obstacle_axes_swapped,
+                                      [(TO.test_single_detour_touches_the_obstacle, "R3", 1.2)]),
+    "obstacle rows missing": ("obstacle_matrix", _obstacle_rows_missing_from_gram,
+                              [(TO.test_gram_and_inverse_closed_forms, 3, 1, 1.0)]),
 }
 
 

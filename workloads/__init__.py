@@ -125,6 +125,50 @@ def sphere_shell(n: int, seed: int, radius: float = 5.0, m: int = 100,
     return Problem(n=n, m=m, T=T, start=start, goal=goal, name=f"shell{n}_s{seed}")
 
 
+def obstacle_box(n: int, n_obs: int, seed: int, box=(6.0, 6.0, 3.0), m: int = 100,
+                 T: float = 8.0, r_range=(0.3, 0.6), min_sep: float = MIN_SEP):
+    """Random start/goal box with static spherical obstacles (the paper's
+    random-obstacle benchmark, Sec. IV): obstacle centres uniform in the box,
+    radii uniform in r_range; each obstacle row holds the centre and the
+    semi-axes of the combined agent-obstacle spheroid (l_xy/2 + r, l_z/2 + r).
+    Starts and goals are rejection-sampled like random_box and also kept 0.2 m
+    outside every combined spheroid.  Returns (Problem, obstacles (n_obs, 5)
+    float32)."""
+    rng = np.random.default_rng(seed)
+    lo = np.zeros(3)
+    hi = np.asarray(box, np.float64)
+    cen = lo + (hi - lo) * rng.random((n_obs, 3))
+    rad = r_range[0] + (r_range[1] - r_range[0]) * rng.random(n_obs)
+    ax = A_XY / 2 + rad
+    bz = B_Z / 2 + rad
+
+    def clear(c):
+        if n_obs == 0:
+            return True
+        q = ((c[0] - cen[:, 0]) ** 2 + (c[1] - cen[:, 1]) ** 2) / (ax + 0.2) ** 2 + \
+            (c[2] - cen[:, 2]) ** 2 / (bz + 0.2) ** 2
+        return bool(q.min() >= 1.0)
+
+    def sample():
+        pts = np.empty((n, 3))
+        k = tries = 0
+        while k < n:
+            tries += 1
+            if tries > 200000:
+                raise RuntimeError("obstacle sampler could not place all agents")
+            c = lo + (hi - lo) * rng.random(3)
+            if (k == 0 or np.sqrt(((pts[:k] - c) ** 2).sum(axis=1)).min() >= min_sep) and clear(c):
+                pts[k] = c
+                k += 1
+        return pts
+
+    s = sample()
+    g = sample()
+    ob = np.concatenate([cen, ax[:, None], bz[:, None]], axis=1)
+    return (Problem(n=n, m=m, T=T, start=_f32(s), goal=_f32(g), name=f"obst{n}x{n_obs}_s{seed}"),
+            _f32(ob))
+
+
 # ---------------------------------------------------------------------------
 # The five workload configurations.
 # ---------------------------------------------------------------------------
