@@ -109,6 +109,17 @@ typedef struct {
     double rho_growth;     /* > 0 when rho_stages > 1 */
     int rho_stage_iters;   /* >= 1 when rho_stages > 1 */
     int multipliers;       /* AMTO_MULT_*: how lambda is kept between iterations */
+    /* Static obstacles per instance (Sec. IV-A: obstacles by their
+     * circumscribing spheres, only the A_fc^T b_fc work grows with their
+     * number): each (agent, obstacle, sample) is one more row of A_fc with a
+     * fixed partner, the obstacle centre, projected on the combined
+     * agent-obstacle spheroid given per obstacle (amto_set_obstacles).  The
+     * penalty adds n_obstacles rho P^T P per agent to the KKT matrix, so the
+     * cached inverse is the plan's.  0..64.  Plans with obstacles run the
+     * graph loop with the batched, tensor-core or structured apply (not the
+     * block solver, not the fused apply); mixed batches, the server and
+     * amto_solve_static take plans without obstacles. */
+    int n_obstacles;
 } amto_params;
 
 /* How the multipliers lambda (Eq. lag_update) are kept between iterations.
@@ -179,6 +190,7 @@ typedef struct {
     int apply_mode;                     /* AMTO_APPLY_BATCHED, _FUSED or _KRONECKER */
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
     int multipliers;                    /* AMTO_MULT_PAIRS or AMTO_MULT_AGGREGATE */
+    int n_obstacles;                    /* static obstacles per instance */
 } amto_info;
 
 /*
@@ -281,6 +293,21 @@ amto_status amto_solve_static(amto_plan plan, const float* start, const float* g
 amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out,
                            float* alpha_out, float* beta_out, float* d_out,
                            void* stream);
+
+/*
+ * amto_set_obstacles - the static obstacles of instances 0..batch-1 for the
+ * plan's later solves (reading R-obst): device array [batch][n_obstacles][5]
+ * of float32 (centre x, y, z, then the semi-axes l_xy, l_z of the combined
+ * agent-obstacle spheroid, e.g. agent half-extent plus obstacle radius).
+ * Copied asynchronously on `stream` into the plan (the caller may reuse the
+ * array once the stream has passed this call).  A solve of a plan with
+ * obstacles needs them set for all of its instances (else EINVAL); an
+ * instance with a non-finite value or a semi-axis <= 0 is flagged non-finite
+ * by the solve (residual NaN, iterations -1).  lambda_init of a warm start
+ * covers the pairs only; the obstacle multipliers start at 0.  EINVAL if the
+ * plan has no obstacles or batch is outside [1, max_batch].
+ */
+amto_status amto_set_obstacles(amto_plan plan, int batch, const float* obstacles, void* stream);
 
 /* Sizes and self-check figures of a plan (host struct, synchronous). */
 amto_status amto_get_info(amto_plan plan, amto_info* out);

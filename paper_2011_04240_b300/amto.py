@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
                 ("tile_group", ctypes.c_int), ("tile_time_blocks", ctypes.c_int),
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
-                ("rho_stage_iters", ctypes.c_int), ("multipliers", ctypes.c_int)]
+                ("rho_stage_iters", ctypes.c_int), ("multipliers", ctypes.c_int),
+                ("n_obstacles", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -56,7 +57,7 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
                 ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
-                ("multipliers", ctypes.c_int)]
+                ("multipliers", ctypes.c_int), ("n_obstacles", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -105,6 +106,7 @@ SIGNATURES = {
     "amto_solve_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_float, _P, _P, _P,
                                          _P]),
     "amto_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "amto_set_obstacles": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "amto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "amto_get_kkt_inverse": (ctypes.c_int, [_P, _P]),
     "amto_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
@@ -256,14 +258,15 @@ class Planner:
                  proj_mode: int = PROJ_LITERAL, precision: int = PREC_FP32,
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
                  apply_mode: int = 0, loop_mode: int = 0, rho_stages: int = 0,
-                 rho_growth: float = 1.0, rho_stage_iters: int = 1, multipliers: int = 0):
+                 rho_growth: float = 1.0, rho_stage_iters: int = 1, multipliers: int = 0,
+                 n_obstacles: int = 0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
                              apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters,
-                             multipliers)
+                             multipliers, n_obstacles)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)
@@ -318,6 +321,13 @@ class Planner:
               _ptr(iters), self._stream(stream))
         self.last_batch = B
         return xi, resid, iters
+
+    def set_obstacles(self, obstacles, stream=None):
+        """Static obstacles [B, n_obstacles, 5] (centre x, y, z, l_xy, l_z of the
+        combined agent-obstacle spheroid) for the instances of later solves."""
+        B = obstacles.shape[0]
+        self._check_tensor(obstacles, (B, self.params.n_obstacles, 5), "obstacles")
+        _check(load().amto_set_obstacles(self.plan, B, _ptr(obstacles), self._stream(stream)))
 
     def state(self, stream=None):
         """(lambda [B,3,p,m], alpha, beta, d [B,p,m]) of the last solve; lambda

@@ -110,20 +110,22 @@ struct PairGeom {
     int TPW;        // time samples per warp pass = 32 / G
     int nbk;        // agent blocks = ceil(n / G)
     int npad;       // nbk * G
-    int S;          // steps per time group = nbk^2 G / 2 (a multiple of 4)
+    int S;          // pair steps per time group = nbk^2 G / 2 (a multiple of 4)
+    int So;         // agent-obstacle steps per time group = nbk n_obs rounded up to 4
     int warps;      // warps per block
     int QW;         // time groups per warp
     int QC;         // time groups per block = warps * QW
     int TC;         // time samples per block = QC * TPW
     int n_chunks;   // work units per instance = ceil(m / TC)
     int MQ;         // time groups per instance = n_chunks * QC
-    long long lam_floats;  // multiplier floats per instance and buffer = MQ * S * 3 * 32
+    long long lam_floats;  // multiplier floats per instance and buffer = MQ * (S + So) * 3 * 32
     int grid;       // persistent pair-kernel blocks (set when the kernels are configured)
 };
 
 // Pair-kernel geometry for n agents and m samples: lane group G and time
 // blocks per warp and unit QW (0: automatic, depending on the batch size).
-PairGeom choose_geometry(int n, int m, int G_req, int QW_req, int max_batch, bool agg);
+PairGeom choose_geometry(int n, int m, int G_req, int QW_req, int max_batch, bool agg,
+                         int n_obs = 0);
 
 struct Graph {
     cudaGraph_t graph = nullptr;
@@ -167,6 +169,8 @@ struct amto_plan_s {
     float* beq = nullptr;      // [B][3][n nb]
     float* lam[2] = {nullptr, nullptr};  // [B][lam_floats] (PAIRS form only)
     float* Lagg = nullptr;     // [B][3][n nv] A_fc^T lambda (AGGREGATE form only)
+    float* obst = nullptr;     // [B][n_obs][5] obstacle centres and semi-axes (amto_set_obstacles)
+    int obst_batch = 0;        // instances whose obstacles have been set
     float* gpart = nullptr;    // [B][n_chunks][3][n nv]
     float* rpart = nullptr;    // [B][n_chunks]
     float* rhs = nullptr;      // [B][3][kp] (TF32-rounded in tensor-core modes)
@@ -202,7 +206,7 @@ namespace amto {
 // precompute.cu
 // Dynamic shared memory of the pair kernel for a tile (n agents, nv
 // coefficients, nb boundary rows, TC samples per unit, npad padded agents).
-size_t pair_smem_bytes_host(int n, int nv, int nb, int TC, int npad, bool fused);
+size_t pair_smem_bytes_host(int n, int nv, int nb, int TC, int npad, bool fused, int n_obs);
 // Whether a plan with these parameters applies K^-1 inside the pair kernel.
 bool apply_fused(const amto_params& p);
 // Checks of amto_params (no CUDA call); sets the error text on failure.

@@ -54,7 +54,7 @@ void free_plan(amto_plan_s* pl) {
     }
     pl->graphs.clear();
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kag, pl->Kinv64, pl->Ktop,
-                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->gpart, pl->rpart, pl->rhs,
+                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->obst, pl->gpart, pl->rpart, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
                     pl->gemm_tk, pl->ctl, pl->l2_flush};
@@ -209,6 +209,10 @@ amto_status validate_params(const amto_params& p) {
     if (p.loop_mode == AMTO_LOOP_BLOCK && p.apply_mode != AMTO_APPLY_KRONECKER &&
         (p.precision != AMTO_PREC_FP32 || p.apply_mode == AMTO_APPLY_FUSED))
         return einval("the block solver applies K^-1 in float32 (dense or structured) only");
+    if (p.n_obstacles < 0 || p.n_obstacles > 64) return einval("n_obstacles must be in [0, 64]");
+    if (p.n_obstacles > 0 && (p.loop_mode == AMTO_LOOP_BLOCK || p.apply_mode == AMTO_APPLY_FUSED))
+        return einval("plans with obstacles run the graph loop with the batched, tensor-core or "
+                      "structured apply");
     if (p.multipliers < AMTO_MULT_AUTO || p.multipliers > AMTO_MULT_AGGREGATE)
         return einval("multipliers must be one of AMTO_MULT_*");
     if (p.multipliers == AMTO_MULT_AGGREGATE) {
@@ -225,9 +229,9 @@ amto_status validate_params(const amto_params& p) {
         return einval("tile_time_blocks must be in [0, 8]");
     {
         const PairGeom g = choose_geometry(p.n_agents, p.m_steps, p.tile_group, p.tile_time_blocks,
-                                           p.max_batch, mult_aggregate(p));
+                                           p.max_batch, mult_aggregate(p), p.n_obstacles);
         if (pair_smem_bytes_host(p.n_agents, p.poly_degree + 1, __builtin_popcount(p.bc_mask),
-                                 g.TC, g.npad, apply_fused(p)) > 227 * 1024)
+                                 g.TC, g.npad, apply_fused(p), p.n_obstacles) > 227 * 1024)
             return einval("the pair-kernel tile does not fit in shared memory; use fewer "
                           "time blocks per warp");
         if (p.loop_mode == AMTO_LOOP_BLOCK &&
@@ -277,7 +281,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
     pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch,
-                              mult_aggregate(p));
+                              mult_aggregate(p), p.n_obstacles);
     pl->fused = apply_fused(p);
     {
         RhoSched& sc = pl->sched;
@@ -334,6 +338,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     ALLOC(pl->xi, (size_t)B * 3 * nvn);
     ALLOC(pl->beq, (size_t)B * 3 * n * nb);
+    if (p.n_obstacles > 0) ALLOC(pl->obst, (size_t)B * p.n_obstacles * 5);
     if (pl->agg) {
         ALLOC(pl->Lagg, (size_t)B * 3 * nvn);
     } else {
@@ -404,6 +409,8 @@ amto_status amto_solve(amto_plan plan, int batch, const float* start, const floa
     if (!start || !goal || !xi_out) return einval("start, goal and xi_out are required");
     if (max_iters < 0) return einval("max_iters must be >= 0");
     if (!(tol >= 0.f) || !std::isfinite(tol)) return einval("tol must be a finite value >= 0");
+    if (plan->prm.n_obstacles > 0 && batch > plan->obst_batch)
+        return einval("the obstacles of this batch's instances have not been set (amto_set_obstacles)");
     DeviceGuard g(plan->device);
     if (!g.ok) {
         set_error("cannot select the plan's device");
@@ -454,6 +461,20 @@ amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out, float* 
     return launch_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, (cudaStream_t)stream);
 }
 
+amto_status amto_set_obstacles(amto_plan plan, int batch, const float* obstacles, void* stream) {
+    clear_error();
+    if (!plan) return einval("plan is NULL");
+    if (plan->prm.n_obstacles == 0) return einval("the plan has no obstacles (n_obstacles = 0)");
+    if (batch < 1 || batch > plan->prm.max_batch) return einval("batch must be in [1, max_batch]");
+    if (!obstacles) return einval("obstacles is NULL");
+    DeviceGuard g(plan->device);
+    AMTO_CUDA_TRY(cudaMemcpyAsync(plan->obst, obstacles,
+                                  sizeof(float) * 5 * (size_t)batch * plan->prm.n_obstacles,
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    if (batch > plan->obst_batch) plan->obst_batch = batch;
+    return AMTO_OK;
+}
+
 amto_status amto_get_info(amto_plan plan, amto_info* out) {
     clear_error();
     if (!plan || !out) return einval("plan and out are required");
@@ -475,6 +496,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
                     : plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
     out->loop_mode = plan->block ? AMTO_LOOP_BLOCK : AMTO_LOOP_GRAPH;
     out->multipliers = plan->agg ? AMTO_MULT_AGGREGATE : AMTO_MULT_PAIRS;
+    out->n_obstacles = plan->prm.n_obstacles;
     if (plan->block) {
         out->launches_per_iteration = 0;
         out->launches_fixed = 5;  // setup, initial projection, block solver, residual, outputs

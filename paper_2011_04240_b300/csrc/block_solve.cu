@@ -453,7 +453,8 @@ bool loop_block(const amto_params& p) {
     if (p.loop_mode == AMTO_LOOP_BLOCK) return true;
     if (p.loop_mode == AMTO_LOOP_GRAPH) return false;
     return p.precision == AMTO_PREC_FP32 && p.apply_mode != AMTO_APPLY_FUSED &&
-           p.multipliers != AMTO_MULT_AGGREGATE && p.n_agents <= 8 && p.max_batch <= 148;
+           p.multipliers != AMTO_MULT_AGGREGATE && p.n_obstacles == 0 && p.n_agents <= 8 &&
+           p.max_batch <= 148;
 }
 
 bool mult_aggregate(const amto_params& p) {

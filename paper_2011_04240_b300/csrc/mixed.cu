@@ -166,6 +166,10 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, a
                       "m_steps, poly_degree, T, a, b, rho, bc_mask and proj_mode");
             return AMTO_EINVAL;
         }
+        if (a->prm.n_obstacles > 0) {
+            set_error("invalid argument: mixed batches take plans without obstacles");
+            return AMTO_EINVAL;
+        }
         bool same_sched = a->sched.J == z->sched.J && a->sched.E == z->sched.E;
         for (int j = 0; same_sched && j < a->sched.J; ++j)
             same_sched = a->sched.rho_d[j] == z->sched.rho_d[j];

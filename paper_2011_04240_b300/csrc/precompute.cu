@@ -81,7 +81,10 @@ __global__ void k_small(int m, int nv, unsigned mask, const double* P, const dou
 // B_qi = +P / -P for the first / second agent of pair q (Eq. A_f): every
 // agent is in n-1 pairs, so the diagonal block is (n-1) P^T P, and two
 // different agents share one pair with opposite signs, giving -P^T P.
-__global__ void k_assemble(int n, int nv, int nb, double rho, const double* PtP,
+// Full KKT matrix of Eq. (kkt_step_x): every agent is in n - 1 pairs and
+// n_obs agent-obstacle rows (reading R-obst), so its diagonal block carries
+// rho (n - 1 + n_obs) P^T P and every pair -rho P^T P off the diagonal.
+__global__ void k_assemble(int n, int n_obs, int nv, int nb, double rho, const double* PtP,
                            const double* DtD, const double* A, double* K) {
     int kdim = n * (nv + nb);
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,7 +94,8 @@ __global__ void k_assemble(int n, int nv, int nb, double rho, const double* PtP,
     double v = 0.0;
     if (r < nvn && c < nvn) {
         int i = r / nv, k = r % nv, j = c / nv, l = c % nv;
-        v = (i == j) ? DtD[k * nv + l] + rho * (n - 1) * PtP[k * nv + l] : -rho * PtP[k * nv + l];
+        v = (i == j) ? DtD[k * nv + l] + rho * (n - 1 + n_obs) * PtP[k * nv + l]
+                     : -rho * PtP[k * nv + l];
     } else if (r < nvn) {
         int cc = c - nvn, j = cc / nb, rr = cc % nb, i = r / nv, k = r % nv;
         v = (i == j) ? A[rr * nv + k] : 0.0;
@@ -298,7 +302,7 @@ amto_status precompute(amto_plan_s* pl) {
     cudaStream_t s = pl->cap_stream;
     double *P = nullptr, *dP = nullptr, *ddP = nullptr, *PtP = nullptr, *DtD = nullptr,
            *A = nullptr, *K = nullptr, *W = nullptr, *K0 = nullptr, *K0inv = nullptr,
-           *Kn = nullptr, *Kninv = nullptr, *sd = nullptr;
+           *Kn = nullptr, *Kninv = nullptr, *Ko = nullptr, *Koinv = nullptr, *sd = nullptr;
     int* si = nullptr;
     unsigned long long* err = nullptr;
     amto_status st = AMTO_OK;
@@ -321,6 +325,8 @@ amto_status precompute(amto_plan_s* pl) {
     PC_ALLOC(K0inv, sizeof(double) * (nv + nb) * (nv + nb));
     PC_ALLOC(Kn, sizeof(double) * (nv + nb) * (nv + nb));
     PC_ALLOC(Kninv, sizeof(double) * (nv + nb) * (nv + nb));
+    PC_ALLOC(Ko, sizeof(double) * (nv + nb) * (nv + nb));
+    PC_ALLOC(Koinv, sizeof(double) * (nv + nb) * (nv + nb));
     PC_ALLOC(sd, sizeof(double) * 4);
     PC_ALLOC(si, sizeof(int) * 4);
     PC_ALLOC(err, sizeof(unsigned long long));
@@ -344,15 +350,23 @@ amto_status precompute(amto_plan_s* pl) {
     double worst = 0.0;
     for (int j = pl->sched.J - 1; j >= 0 && st == AMTO_OK; --j) {
         const double rho = pl->sched.rho_d[j];
-        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, nv, nb, rho, PtP, DtD,
-                                                                       A, K);
-        k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * n, A, Kn);
+        const int n_obs = pl->prm.n_obstacles;
+        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, n_obs, nv, nb, rho, PtP,
+                                                                       DtD, A, K);
+        // agent-level blocks of the structured inverse: the relative motion
+        // sees rho (n + n_obs) P^T P, the common motion rho n_obs P^T P
+        k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * (n + n_obs), A,
+                                                            Kn);
+        if (n_obs > 0)
+            k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * n_obs, A,
+                                                                Ko);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("precompute kernel launch failed");
             st = AMTO_ECUDA;
             break;
         }
         st = invert(nv + nb, Kn, Kninv, W, si, sd, s);
+        if (st == AMTO_OK && n_obs > 0) st = invert(nv + nb, Ko, Koinv, W, si, sd, s);
         if (st == AMTO_OK) st = invert(kdim, K, pl->Kinv64, W, si, sd, s);
         if (st != AMTO_OK) break;
         cudaMemsetAsync(err, 0, sizeof(unsigned long long), s);
@@ -387,7 +401,7 @@ amto_status precompute(amto_plan_s* pl) {
                 reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi) + j * pl->ks_bf,
                 reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo) + j * pl->ks_bf);
         k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, Kninv, pl->Kag + j * pl->ks_ag);
-        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, K0inv,
+        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, n_obs > 0 ? Koinv : K0inv,
                                                       pl->Kag + j * pl->ks_ag + nv * d);
     }
     pl->kkt_check = worst;
@@ -404,7 +418,7 @@ amto_status precompute(amto_plan_s* pl) {
     }
     cudaFree(P); cudaFree(dP); cudaFree(ddP); cudaFree(PtP); cudaFree(DtD); cudaFree(A);
     cudaFree(K); cudaFree(W); cudaFree(K0); cudaFree(K0inv); cudaFree(Kn); cudaFree(Kninv);
-    cudaFree(sd); cudaFree(si);
+    cudaFree(Ko); cudaFree(Koinv); cudaFree(sd); cudaFree(si);
     cudaFree(err);
     return st;
 }

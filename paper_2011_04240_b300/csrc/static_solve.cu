@@ -72,6 +72,10 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
         set_error("invalid argument: plan is NULL");
         return AMTO_EINVAL;
     }
+    if (plan->prm.n_obstacles > 0) {
+        set_error("invalid argument: amto_solve_static takes plans without obstacles");
+        return AMTO_EINVAL;
+    }
     if (plan->prm.precision != AMTO_PREC_FP32) {
         set_error("invalid argument: amto_solve_static takes plans made with AMTO_PREC_FP32");
         return AMTO_EINVAL;

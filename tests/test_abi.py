@@ -59,7 +59,12 @@ def _params(**kw):
                                  dict(n_agents=256, tile_group=8, tile_time_blocks=8),
                                  dict(apply_mode=4), dict(apply_mode=-1),
                                  dict(apply_mode=2, precision=1), dict(loop_mode=3),
-                                 dict(loop_mode=2, precision=1), dict(loop_mode=2, apply_mode=2)])
+                                 dict(loop_mode=2, precision=1), dict(loop_mode=2, apply_mode=2),
+                                 dict(n_obstacles=-1), dict(n_obstacles=65),
+                                 dict(n_obstacles=2, loop_mode=2),
+                                 dict(n_obstacles=2, apply_mode=2),
+                                 dict(multipliers=3), dict(multipliers=2, proj_mode=0),
+                                 dict(rho_stages=17), dict(rho_stages=3, rho_growth=0.0)])
 def test_create_rejects_invalid_params(lib, bad):
     from paper_2011_04240_b300 import amto
     plan = ctypes.c_void_p()
@@ -76,6 +81,7 @@ def test_null_arguments_rejected(lib):
                           None) == amto.EINVAL
     assert lib.amto_get_info(None, None) == amto.EINVAL
     assert lib.amto_set_trace(None, 1) == amto.EINVAL
+    assert lib.amto_set_obstacles(None, 1, None, None) == amto.EINVAL
     lib.amto_destroy(None)  # no-op
     assert lib.amto_version().decode().startswith("amto")
 
