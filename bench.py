@@ -525,6 +525,43 @@ def precision_report(args, ks=(1, 2, 5, 10, 20, 200), samples=(0, 85, 170, 255))
     return out
 
 
+def obstacle_scaling(counts=(0, 4, 8, 16, 32), B=256, n=16, K=40):
+    """Static obstacles (Sec. IV-A): 256 instances of 16 agents in a 6x6x3 m
+    box with n_obs random spherical obstacles each (literal projection, FP32
+    apply), time per iteration of the graph loop against the obstacle count
+    (the paper reports near-linear growth)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Planner
+    out = []
+    for n_obs in counts:
+        pairs = [W.obstacle_box(n, n_obs, 7000 + i, box=(6.0, 6.0, 3.0)) for i in range(B)]
+        probs = [p for p, _ in pairs]
+        s_np, g_np = W.stack(probs)
+        s = torch.from_numpy(s_np).cuda()
+        g = torch.from_numpy(g_np).cuda()
+        pl = Planner(n, 100, 8.0, max_batch=B, n_obstacles=n_obs)
+        if n_obs:
+            pl.set_obstacles(torch.from_numpy(np.stack([o for _, o in pairs])).cuda())
+        pl.solve(s, g, 3)
+        torch.cuda.synchronize()
+        ts = []
+        for k in (5, 5 + K):
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            pl.solve(s, g, k)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = 1e3 * (ts[1] - ts[0]) / K
+        out.append({"n_obstacles": n_obs, "us_per_iteration": us, "value": B / (us / 1e6)})
+        pl.close()
+    return {"workload": f"{B} x {n} agents, 6x6x3 m box, random spherical obstacles "
+                        "(radius 0.3-0.6 m), literal projection, FP32 apply, m=100",
+            "unit": UNIT, "points": out}
+
+
 def config1_latency(reps=5):
     """4 agents on a 3 m circle, antipodal goals, m = 50, T = 5 s, 200 fixed
     iterations, literal projection, batch 1: wall time of one solve on the
@@ -772,6 +809,7 @@ def main():
             extras["rho_schedule_per_instance"] = plain_per_instance(
                 rho_schedule=(10, 100 ** (1 / 9), 10))
             extras["config1_latency"] = config1_latency()
+            extras["obstacles"] = obstacle_scaling()
             extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:

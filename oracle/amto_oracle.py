@@ -68,6 +68,12 @@ Readings of ambiguous passages (each also listed in the design notes):
             n_obs rho P^T P per agent, so the cached inverse depends on
             (n, n_obs, rho).  Obstacle rows are ordered agent-major, then
             obstacle, then time; lambda^0 = 0 on them; they count in r_max.
+  R-planar  Sec. III's "disks in 2D": agents in the x-y plane are disks of
+            radius l_xy; Delta = (Delta_x, Delta_y), alpha = atan2(Delta_y,
+            Delta_x) (0 when Delta = 0, as R-degen), u = l_xy (cos alpha,
+            sin alpha), d and lambda as in 3-D.  The z axis is dropped: z
+            boundary values are taken as 0, its QP has no pair term, and the
+            z coefficients stay 0.
 """
 from __future__ import annotations
 
@@ -160,6 +166,7 @@ class Matrices:
     Kinv: np.ndarray       # its inverse (Remark 1: computed once)
     n_obs: int = 0         # static obstacles per instance (reading R-obst)
     A_obs: sp.csr_matrix | None = None   # (n n_obs m) x (n nv) agent-obstacle rows
+    planar: bool = False   # disks in the x-y plane (reading R-planar)
 
     @property
     def nv(self):
@@ -187,7 +194,8 @@ def obstacle_matrix(P, n: int, n_obs: int):
 
 
 def build_matrices(n: int, m: int, degree: int, T: float, a: float, b: float,
-                   rho: float, bc_mask: int = BC_ALL, n_obs: int = 0) -> Matrices:
+                   rho: float, bc_mask: int = BC_ALL, n_obs: int = 0,
+                   planar: bool = False) -> Matrices:
     """Assemble Q_x, A_eq, A_fc and the KKT matrix, and invert it (Eq. kkt_step_x).
 
     The inverse is a dense LAPACK LU-based inverse (partial pivoting); it is
@@ -205,7 +213,16 @@ def build_matrices(n: int, m: int, degree: int, T: float, a: float, b: float,
     K = np.block([[H, A_eq.T], [A_eq, np.zeros((nz, nz))]])
     Kinv = np.linalg.inv(K)
     return Matrices(n, m, degree, T, a, b, rho, bc_mask, P, dP, ddP, A, Q, A_eq,
-                    A_fc, K, Kinv, n_obs, A_obs)
+                    A_fc, K, Kinv, n_obs, A_obs, planar)
+
+
+def planar_inputs(start, goal):
+    """Start and goal of a planar problem (reading R-planar): z taken as 0."""
+    s = np.array(start, np.float64, copy=True)
+    g = np.array(goal, np.float64, copy=True)
+    s[:, 2] = 0.0
+    g[:, 2] = 0.0
+    return s, g
 
 
 def boundary_values(start, goal, bc_mask: int = BC_ALL, bc_extra=None):
@@ -266,8 +283,13 @@ def projection(D, lam, M: Matrices, mode: str = "R2", a=None, b=None):
         Wab = D + lam / M.rho
     else:
         Wab = D
-    alpha, beta = alpha_beta(Wab, a, b)
-    U = spheroid_direction(alpha, beta, a, b)
+    if getattr(M, "planar", False):  # disks (reading R-planar): the in-plane angle only
+        alpha = np.arctan2(Wab[1], Wab[0])
+        beta = np.full_like(alpha, np.pi / 2)
+        U = np.stack([a * np.cos(alpha), a * np.sin(alpha), np.zeros_like(alpha)])
+    else:
+        alpha, beta = alpha_beta(Wab, a, b)
+        U = spheroid_direction(alpha, beta, a, b)
     Wd = D if mode == "R3" else D + lam / M.rho
     d = d_step(Wd, U)
     return alpha, beta, d, U
@@ -277,6 +299,9 @@ def target_vector(alpha, beta, d, lam, M: Matrices, a=None, b=None):
     """b_fc of Eq. (b_f) per axis: l d sin/cos terms minus lambda/rho."""
     a = M.a if a is None else a
     b = M.b if b is None else b
+    if getattr(M, "planar", False):
+        U = np.stack([a * np.cos(alpha), a * np.sin(alpha), np.zeros_like(alpha)])
+        return d * U - lam / M.rho
     return d * spheroid_direction(alpha, beta, a, b) - lam / M.rho
 
 

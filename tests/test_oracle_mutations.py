@@ -15,6 +15,7 @@ import tests.test_oracle_convergence as TC
 import tests.test_oracle_kkt as TK
 import tests.test_oracle_projection as TP
 import tests.test_oracle_obstacles as TO
+import tests.test_oracle_planar as TPL
 import tests.test_oracle_qp as TQ
 
 
@@ -76,8 +77,18 @@ def _obstacle_rows_missing_from_gram(P, n, n_obs):
     return _orig["obstacle_matrix"](P, n, 0)
 
 
+def _planar_angle_axes_swapped(D, lam, M, mode="R2", a=None, b=None):
+    if not getattr(M, "planar", False):
+        return _orig["projection"](D, lam, M, mode, a, b)
+    a = M.a if a is None else a
+    alpha = np.arctan2(D[0], D[1])
+    U = np.stack([a * np.cos(alpha), a * np.sin(alpha), np.zeros_like(alpha)])
+    Wd = D if mode == "R3" else D + lam / M.rho
+    return alpha, np.full_like(alpha, np.pi / 2), OA.d_step(Wd, U), U
+
+
 _orig = {k: getattr(OA, k) for k in ["pair_matrix", "alpha_beta", "bernstein_basis",
-                                     "obstacle_rows", "obstacle_matrix"]}
+                                     "obstacle_rows", "obstacle_matrix", "projection"]}
 
 MUTATIONS = {
     "pair signs swapped": ("pair_matrix", _pair_matrix_signs_swapped,
@@ -103,6 +114,8 @@ MUTATIONS = {
                                       [(TO.test_single_detour_touches_the_obstacle, "R3", 1.2)]),
     "obstacle rows missing": ("obstacle_matrix", _obstacle_rows_missing_from_gram,
                               [(TO.test_gram_and_inverse_closed_forms, 3, 1, 1.0)]),
+    "planar angle axes swapped": ("projection", _planar_angle_axes_swapped,
+                                  [(TPL.test_lambda_free_residual_inside_the_disk,)]),
 }
 
 
