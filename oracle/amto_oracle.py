@@ -247,8 +247,19 @@ def boundary_values(start, goal, bc_mask: int = BC_ALL, bc_extra=None):
 # ---------------------------------------------------------------------------
 
 def pair_differences(M: Matrices, xi):
-    """Delta = A_fc c per axis: (3, p*m), xi given as (3, n*nv)."""
-    return np.stack([M.A_fc @ xi[ax] for ax in range(3)])
+    """Delta = A_fc c per axis: (3, p*m), xi given as (3, n*nv).
+
+    Formed as x_i(t) - x_j(t) from the positions (Eqs. A_f, sphere_proposed),
+    so agents with identical coefficients give Delta = 0 exactly and take
+    the R-degen direction (a product with A_fc's +P/-P rows leaves a
+    rounding residue there instead)."""
+    pos = np.einsum("tk,ank->ant", M.P, np.asarray(xi, np.float64).reshape(3, M.n, M.nv))
+    pl = pair_list(M.n)
+    if not pl:
+        return np.zeros((3, 0))
+    ii = np.array([q[0] for q in pl])
+    jj = np.array([q[1] for q in pl])
+    return (pos[:, ii, :] - pos[:, jj, :]).reshape(3, -1)
 
 
 def alpha_beta(D, a: float, b: float):
