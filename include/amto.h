@@ -120,6 +120,12 @@ typedef struct {
      * block solver, not the fused apply); mixed batches, the server and
      * amto_solve_static take plans without obstacles. */
     int n_obstacles;
+    /* 1: agents are disks of radius l_xy in the x-y plane (Sec. III, "disks
+     * in 2D"): alpha = atan2(Delta_y, Delta_x), u = l_xy (cos alpha,
+     * sin alpha), Delta = 0 projects on +x; b (l_z) and every z input (start,
+     * goal, boundary extras, warm starts, obstacle centres and l_z) are
+     * ignored, and the returned z coefficients and multipliers are 0. */
+    int planar;
 } amto_params;
 
 /* How the multipliers lambda (Eq. lag_update) are kept between iterations.
@@ -191,6 +197,7 @@ typedef struct {
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
     int multipliers;                    /* AMTO_MULT_PAIRS or AMTO_MULT_AGGREGATE */
     int n_obstacles;                    /* static obstacles per instance */
+    int planar;                         /* 1: disks in the x-y plane */
 } amto_info;
 
 /*

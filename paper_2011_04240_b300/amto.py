@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
                 ("rho_stage_iters", ctypes.c_int), ("multipliers", ctypes.c_int),
-                ("n_obstacles", ctypes.c_int)]
+                ("n_obstacles", ctypes.c_int), ("planar", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("launches_per_iteration", ctypes.c_int),
                 ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
-                ("multipliers", ctypes.c_int), ("n_obstacles", ctypes.c_int)]
+                ("multipliers", ctypes.c_int), ("n_obstacles", ctypes.c_int),
+                ("planar", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -259,14 +260,14 @@ class Planner:
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
                  apply_mode: int = 0, loop_mode: int = 0, rho_stages: int = 0,
                  rho_growth: float = 1.0, rho_stage_iters: int = 1, multipliers: int = 0,
-                 n_obstacles: int = 0):
+                 n_obstacles: int = 0, planar: int = 0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
                              apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters,
-                             multipliers, n_obstacles)
+                             multipliers, n_obstacles, planar)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)

@@ -104,6 +104,19 @@ struct RhoSched {
     double rho_d[kMaxRhoStages];
 };
 
+// Planar plans (disks in the x-y plane) run the spheroid kernels with the
+// axes permuted: kernel axis 0 holds the plane's y, axis 1 nothing (0), axis 2
+// the plane's x, and l_z = l_xy, so the kernels' degenerate direction +z is
+// the plane's +x (alpha = atan2(0, 0) = 0).  planar_src: the user axis a
+// kernel axis reads (-1: none); planar_dst: the kernel axis a user axis
+// comes from (-1: none, returned as 0).
+__host__ __device__ inline int planar_src(int kernel_axis) {
+    return kernel_axis == 0 ? 1 : kernel_axis == 2 ? 0 : -1;
+}
+__host__ __device__ inline int planar_dst(int user_axis) {
+    return user_axis == 0 ? 2 : user_axis == 1 ? 0 : -1;
+}
+
 // Geometry of the pair kernel's work decomposition (see iterate.cu).
 struct PairGeom {
     int G;          // agents per lane group (8, 16 or 32)

@@ -210,6 +210,7 @@ amto_status validate_params(const amto_params& p) {
         (p.precision != AMTO_PREC_FP32 || p.apply_mode == AMTO_APPLY_FUSED))
         return einval("the block solver applies K^-1 in float32 (dense or structured) only");
     if (p.n_obstacles < 0 || p.n_obstacles > 64) return einval("n_obstacles must be in [0, 64]");
+    if (p.planar != 0 && p.planar != 1) return einval("planar must be 0 or 1");
     if (p.n_obstacles > 0 && (p.loop_mode == AMTO_LOOP_BLOCK || p.apply_mode == AMTO_APPLY_FUSED))
         return einval("plans with obstacles run the graph loop with the batched, tensor-core or "
                       "structured apply");
@@ -257,7 +258,9 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     if (!out) return einval("out is NULL");
     *out = nullptr;
     if (!prm) return einval("params is NULL");
-    const amto_params& p = *prm;
+    amto_params pp = *prm;
+    if (pp.planar == 1) pp.b = pp.a;  // disks: the kernels' l_z is l_xy (z unused)
+    const amto_params& p = pp;
     if (amto::validate_params(p) != AMTO_OK) return AMTO_EINVAL;
 
     amto_plan_s* pl = new (std::nothrow) amto_plan_s();
@@ -461,6 +464,20 @@ amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out, float* 
     return launch_state(plan, batch, lambda_out, alpha_out, beta_out, d_out, (cudaStream_t)stream);
 }
 
+// Obstacles of a planar plan in the kernels' axes: centre (y, 0, x), both
+// semi-axes the disk's radius.
+__global__ void k_planar_obstacles(long long count, const float* in, float* out) {
+    const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= count) return;
+    const float* s = in + o * 5;
+    float* d = out + o * 5;
+    d[0] = s[1];
+    d[1] = 0.f;
+    d[2] = s[0];
+    d[3] = s[3];
+    d[4] = s[3];
+}
+
 amto_status amto_set_obstacles(amto_plan plan, int batch, const float* obstacles, void* stream) {
     clear_error();
     if (!plan) return einval("plan is NULL");
@@ -468,9 +485,15 @@ amto_status amto_set_obstacles(amto_plan plan, int batch, const float* obstacles
     if (batch < 1 || batch > plan->prm.max_batch) return einval("batch must be in [1, max_batch]");
     if (!obstacles) return einval("obstacles is NULL");
     DeviceGuard g(plan->device);
-    AMTO_CUDA_TRY(cudaMemcpyAsync(plan->obst, obstacles,
-                                  sizeof(float) * 5 * (size_t)batch * plan->prm.n_obstacles,
-                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    const long long count = (long long)batch * plan->prm.n_obstacles;
+    if (plan->prm.planar) {
+        k_planar_obstacles<<<(unsigned)((count + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+            count, obstacles, plan->obst);
+        AMTO_CUDA_TRY(cudaGetLastError());
+    } else {
+        AMTO_CUDA_TRY(cudaMemcpyAsync(plan->obst, obstacles, sizeof(float) * 5 * (size_t)count,
+                                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    }
     if (batch > plan->obst_batch) plan->obst_batch = batch;
     return AMTO_OK;
 }
@@ -497,6 +520,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->loop_mode = plan->block ? AMTO_LOOP_BLOCK : AMTO_LOOP_GRAPH;
     out->multipliers = plan->agg ? AMTO_MULT_AGGREGATE : AMTO_MULT_PAIRS;
     out->n_obstacles = plan->prm.n_obstacles;
+    out->planar = plan->prm.planar;
     if (plan->block) {
         out->launches_per_iteration = 0;
         out->launches_fixed = 5;  // setup, initial projection, block solver, residual, outputs

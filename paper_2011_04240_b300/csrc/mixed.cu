@@ -161,9 +161,10 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, a
         }
         if (a->device != z->device || a->m != z->m || a->N != z->N || a->prm.T != z->prm.T ||
             a->prm.a != z->prm.a || a->prm.b != z->prm.b || a->prm.rho != z->prm.rho ||
-            a->prm.bc_mask != z->prm.bc_mask || a->prm.proj_mode != z->prm.proj_mode) {
+            a->prm.bc_mask != z->prm.bc_mask || a->prm.proj_mode != z->prm.proj_mode ||
+            a->prm.planar != z->prm.planar) {
             set_error("invalid argument: the plans of a mixed batch must agree on device, "
-                      "m_steps, poly_degree, T, a, b, rho, bc_mask and proj_mode");
+                      "m_steps, poly_degree, T, a, b, rho, bc_mask, proj_mode and planar");
             return AMTO_EINVAL;
         }
         if (a->prm.n_obstacles > 0) {

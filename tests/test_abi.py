@@ -64,7 +64,8 @@ def _params(**kw):
                                  dict(n_obstacles=2, loop_mode=2),
                                  dict(n_obstacles=2, apply_mode=2),
                                  dict(multipliers=3), dict(multipliers=2, proj_mode=0),
-                                 dict(rho_stages=17), dict(rho_stages=3, rho_growth=0.0)])
+                                 dict(rho_stages=17), dict(rho_stages=3, rho_growth=0.0),
+                                 dict(planar=2), dict(planar=1, a=0.0)])
 def test_create_rejects_invalid_params(lib, bad):
     from paper_2011_04240_b300 import amto
     plan = ctypes.c_void_p()
