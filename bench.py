@@ -562,6 +562,38 @@ def obstacle_scaling(counts=(0, 4, 8, 16, 32), B=256, n=16, K=40):
             "unit": UNIT, "points": out}
 
 
+def planar_compare(B=256, n=32, K=40):
+    """Disks in the plane against spheroids in space: 256 instances of 32
+    agents, 12 x 12 m (x 6 m) random boxes, literal projection, TF32X3 apply;
+    time per iteration of the graph loop."""
+    import torch
+    import workloads as W
+    from paper_2011_04240_b300 import Planner, amto
+    out = {}
+    for planar, box in ((0, (12.0, 12.0, 6.0)), (1, (12.0, 12.0, 0.0))):
+        probs = [W.random_box(n, 8000 + i, box=box) for i in range(B)]
+        s_np, g_np = W.stack(probs)
+        s = torch.from_numpy(s_np).cuda()
+        g = torch.from_numpy(g_np).cuda()
+        pl = Planner(n, 100, 8.0, max_batch=B, planar=planar, precision=amto.PREC_TF32X3)
+        pl.solve(s, g, 3)
+        torch.cuda.synchronize()
+        ts = []
+        for k in (5, 5 + K):
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            pl.solve(s, g, k)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = 1e3 * (ts[1] - ts[0]) / K
+        out["planar" if planar else "spheroids"] = {"us_per_iteration": us,
+                                                    "value": B / (us / 1e6)}
+        pl.close()
+    return {"workload": f"{B} x {n} agents, random 12x12 m plane / 12x12x6 m box, m=100, "
+                        "literal projection, TF32X3 apply", "unit": UNIT, **out}
+
+
 def config1_latency(reps=5):
     """4 agents on a 3 m circle, antipodal goals, m = 50, T = 5 s, 200 fixed
     iterations, literal projection, batch 1: wall time of one solve on the
@@ -810,6 +842,7 @@ def main():
                 rho_schedule=(10, 100 ** (1 / 9), 10))
             extras["config1_latency"] = config1_latency()
             extras["obstacles"] = obstacle_scaling()
+            extras["planar"] = planar_compare()
             extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:

@@ -160,3 +160,19 @@ def test_planar_state_read_back():
     da = np.angle(np.exp(1j * (al[0].ravel() - st.alpha)))
     assert np.abs(da[big]).max() < 1e-3
     np.testing.assert_allclose(d[0].ravel(), st.d, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("mode", ["R2", "R3"])
+def test_sphere_agents(mode):
+    """The sphere specialization (l_xy = l_z) of the 3-D spheroid path."""
+    from paper_2011_04240_b300 import Planner
+    prob = W.random_box(12, 77, box=(6.0, 6.0, 3.0), m=50, T=5.0)
+    pl = Planner(prob.n, prob.m, prob.T, 0.8, 0.8, prob.rho, prob.degree,
+                 proj_mode=MODES[mode], loop_mode=1)
+    s, g = W.stack([prob])
+    import torch
+    xi, r, kk = pl.solve(to_dev(s, pl.device), to_dev(g, pl.device), 25)
+    torch.cuda.synchronize()
+    M = O.build_matrices(prob.n, prob.m, prob.degree, prob.T, 0.8, 0.8, prob.rho)
+    st = O.solve(M, prob.start, prob.goal, 25, mode=mode)
+    assert rel_inf(xi.cpu().numpy()[0].reshape(3, -1), st.xi) < XI_TOL
