@@ -93,7 +93,7 @@ struct Ctl {
 // projection, lambda = 0) to stage 0.
 constexpr int kMaxRhoStages = 16;
 __host__ __device__ inline int rho_stage_of(int k, int J, int E) {
-    if (k < 1) return 0;
+    if (k < 1 || J <= 1) return 0;  // constant rho: no division
     const int s = (k - 1) / E;
     return s < J - 1 ? s : J - 1;
 }
