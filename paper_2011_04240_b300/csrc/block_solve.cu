@@ -84,14 +84,14 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
                                            float& l0, float& l1,
                                            float& l2, float& t0, float& t1, float& t2,
                                            float& fsq) {
+    dz = __fmaf_rn(sgb, 1e-18f, dz);  // Delta = 0 -> sigma l_z e_z, as the batched kernel
     const float s2 = __fmaf_rn(__fmul_rn(dz, dz), ib2,
                                __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), ia2));
-    const float dm = (s2 > FLT_MIN) ? 0.f : 1.f;
     const float is = rsqrtf(fmaxf(s2, FLT_MIN));
     float fx, fy, fz;
     if (LIT) {
         const float ux = __fmul_rn(dx, is), uy = __fmul_rn(dy, is);
-        const float uz = __fmaf_rn(dm, sgb, __fmul_rn(dz, is));
+        const float uz = __fmul_rn(dz, is);
         const float uu = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, __fmul_rn(uz, uz)));
         const float wx = __fmaf_rn(l0, rinv, dx), wy = __fmaf_rn(l1, rinv, dy);
         const float wz = __fmaf_rn(l2, rinv, dz);
@@ -104,7 +104,7 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
         const float k = fminf(0.f, 1.f - is);
         fx = __fmul_rn(dx, k);
         fy = __fmul_rn(dy, k);
-        fz = __fmaf_rn(dm, -sgb, __fmul_rn(dz, k));
+        fz = __fmul_rn(dz, k);
     }
     l0 = __fmaf_rn(rho, fx, l0);
     l1 = __fmaf_rn(rho, fy, l1);
