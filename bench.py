@@ -83,7 +83,7 @@ def serving_problem(n, problem_seed):
     return _serve_pool[key]
 
 
-def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
+def serving_compare(rate, seconds, precision, seed=0, seq_cap=400, rho_schedule=None):
     """One serving run at `rate` req/s: Poisson arrivals over `seconds` of
     single problems with agent counts uniform in {8,16,32,48,64} (degree 10,
     m = 100, random 8x8x4 m box), each solved to max residual < 1e-2 (or the
@@ -102,20 +102,33 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400):
         p = serving_problem(n, ps)
         arr.append((t, p.start, p.goal))
     warm = [W.random_box(n, 99991 + n, box=(8.0, 8.0, 4.0)) for n in SERVE_SIZES]
-    sv = Server(SERVE_SIZES, m_steps=100, T=8.0, proj_mode=amto.PROJ_LITERAL, precision=prec,
-                max_slots=256, chunk_iters=8, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL)
-    try:
-        for p in warm:
-            t = sv.submit(p.start, p.goal)
-            while sv.poll(t, 1000) is None:
-                pass
-        slots = sv.stats()["slots"]
-        recs, wall = SV.run_arrivals(sv, arr, keep_xi=False)
-    finally:
-        sv.close()
+
+    def serve(**kw):
+        sv = Server(SERVE_SIZES, m_steps=100, T=8.0, proj_mode=amto.PROJ_LITERAL,
+                    precision=prec, max_slots=256, chunk_iters=8, max_iters=SERVE_MAX_ITERS,
+                    tol=SERVE_TOL, **kw)
+        try:
+            for p in warm:
+                t = sv.submit(p.start, p.goal)
+                while sv.poll(t, 1000) is None:
+                    pass
+            slots = sv.stats()["slots"]
+            recs, wall = SV.run_arrivals(sv, arr, keep_xi=False)
+        finally:
+            sv.close()
+        return recs, wall, slots
+
+    recs, wall, slots = serve()
     out = {"rate_req_s": rate, "window_s": seconds, "iteration_cap": SERVE_MAX_ITERS,
            "server": dict(SV.summarize(recs, wall, SERVE_MAX_ITERS), apply_precision=precision,
                           slots={str(k): v for k, v in slots.items()})}
+    if rho_schedule:
+        J, gr, E = rho_schedule
+        recs_s, wall_s, _ = serve(rho_stages=J, rho_growth=gr, rho_stage_iters=E)
+        out["server_rho_schedule"] = dict(
+            SV.summarize(recs_s, wall_s, SERVE_MAX_ITERS),
+            schedule=f"rho = {gr:.4g}^j for j < {J}, {E} solves per stage, per request; "
+                     "structured K^-1 apply (each slot at its own stage)")
     planners = {n: Planner(n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, max_batch=1)
                 for n in SERVE_SIZES}
     try:
@@ -843,7 +856,8 @@ def main():
             extras["config1_latency"] = config1_latency()
             extras["obstacles"] = obstacle_scaling()
             extras["planar"] = planar_compare()
-            extras["serving"] = serving_compare(1000.0, 2.0, args.precision)
+            extras["serving"] = serving_compare(1000.0, 2.0, args.precision,
+                                                rho_schedule=(10, 100 ** (1 / 9), 10))
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

@@ -103,8 +103,8 @@ typedef struct {
      * stage min(rho_stages - 1, (k - 1) / rho_stage_iters), the multipliers
      * carry over.  One cached inverse per stage.  rho_stages 0 or 1: constant
      * rho.  A batch iterates in step (every instance of a solve is at the same
-     * k), so the stages switch for the whole batch; the serving layer uses a
-     * constant rho. */
+     * k), so the stages switch for the whole batch; the serving layer's slots
+     * each follow their own (see amto_server_params). */
     int rho_stages;        /* 0..16 */
     double rho_growth;     /* > 0 when rho_stages > 1 */
     int rho_stage_iters;   /* >= 1 when rho_stages > 1 */
@@ -464,6 +464,13 @@ typedef struct {
                               the number of instances whose state fits in it (at most
                               max_slots).  Each count's cached inverse and the plan's
                               fixed buffers come on top of the budget. */
+    /* Increasing rho per request (as amto_params; 0 or 1: constant rho).  The
+     * slots are not in step, so each request follows the schedule from its
+     * own QP count; the server then applies K^-1 in its structured form
+     * (AMTO_APPLY_KRONECKER), whose stage is chosen per instance. */
+    int rho_stages;
+    double rho_growth;
+    int rho_stage_iters;
 } amto_server_params;
 
 typedef struct {

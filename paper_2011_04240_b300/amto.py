@@ -68,7 +68,9 @@ class ServerParams(ctypes.Structure):
                 ("rho", ctypes.c_double), ("proj_mode", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_slots", ctypes.c_int),
                 ("chunk_iters", ctypes.c_int), ("max_iters", ctypes.c_int),
-                ("tol", ctypes.c_float), ("memory_budget", ctypes.c_size_t)]
+                ("tol", ctypes.c_float), ("memory_budget", ctypes.c_size_t),
+                ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
+                ("rho_stage_iters", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -435,7 +437,8 @@ class Server:
 
     def __init__(self, sizes, m_steps=100, T=8.0, a=0.6, b=1.2, rho=1.0, poly_degree=10,
                  proj_mode=PROJ_LITERAL, precision=PREC_FP32, max_slots=64, chunk_iters=8,
-                 max_iters=2000, tol=1e-2, memory_budget=0):
+                 max_iters=2000, tol=1e-2, memory_budget=0, rho_stages=0, rho_growth=1.0,
+                 rho_stage_iters=1):
         import numpy as np
         self._np = np
         self.sizes = [int(x) for x in sizes]
@@ -443,7 +446,8 @@ class Server:
         arr = (ctypes.c_int * len(self.sizes))(*self.sizes)
         self._sizes_arr = arr
         prm = ServerParams(len(self.sizes), arr, m_steps, poly_degree, T, a, b, rho, proj_mode,
-                           precision, max_slots, chunk_iters, max_iters, tol, memory_budget)
+                           precision, max_slots, chunk_iters, max_iters, tol, memory_budget,
+                           rho_stages, rho_growth, rho_stage_iters)
         h = _P()
         _check(load().amto_server_create(ctypes.byref(prm), ctypes.byref(h)))
         self.handle = h.value

@@ -144,6 +144,11 @@ amto_params plan_params(const amto_server_params& p, int n, int slots) {
     ap.proj_mode = p.proj_mode;
     ap.precision = p.precision;
     ap.max_batch = slots;
+    ap.rho_stages = p.rho_stages;
+    ap.rho_growth = p.rho_growth;
+    ap.rho_stage_iters = p.rho_stage_iters;
+    // slots are not in step: the structured apply picks each instance's stage
+    if (p.rho_stages > 1) ap.apply_mode = AMTO_APPLY_KRONECKER;
     return ap;
 }
 

@@ -9,6 +9,7 @@ must stop by the rule of Algorithm 1 (residual below tol, or max_iters).
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 from tests.gpu_helpers import oracle_mats, oracle_solve, planner, gpu_solve, rel_inf
 
@@ -96,6 +97,45 @@ def test_fixed_iterations_match_oracle_and_batch_solve():
         assert rel_inf(res[tk[1]]["xi"], xs[0]) < 1e-5
     finally:
         sv.close()
+
+
+def test_rho_schedule_per_request():
+    """Increasing rho in the server: each request follows the schedule from its
+    own QP count although the slots are not in step (staggered submissions);
+    results match the oracle's scheduled solve, and to the tolerance the
+    requests need fewer iterations than at constant rho."""
+    import time
+    J, g, E = 4, 3.0, 3
+    sv = _server((5, 12), "fp32", max_iters=11, tol=0.0, chunk_iters=2, rho_stages=J,
+                 rho_growth=g, rho_stage_iters=E)
+    try:
+        probs = [W.random_box(5 if i % 2 else 12, 950 + i, box=(8.0, 8.0, 4.0)) for i in range(6)]
+        tk = []
+        for p in probs:
+            tk.append(sv.submit(p.start, p.goal))
+            time.sleep(0.002)  # let earlier requests run a chunk first
+        res = _collect(sv, tk)
+        for t, p in zip(tk, probs):
+            Ms = [O.build_matrices(p.n, p.m, p.degree, p.T, p.a, p.b, p.rho * g ** j)
+                  for j in range(J)]
+            st = O.solve_schedule(Ms, E, p.start, p.goal, 11)
+            assert res[t]["iters"] == 11
+            assert rel_inf(res[t]["xi"].reshape(3, -1), st.xi) < 1e-4
+    finally:
+        sv.close()
+    probs = [W.config2(i) for i in range(4)]
+    iters = {}
+    for sched in (False, True):
+        kw = dict(rho_stages=10, rho_growth=100 ** (1 / 9), rho_stage_iters=10) if sched else {}
+        sv = _server((16,), "fp32", max_iters=500, tol=1e-2, **kw)
+        try:
+            tk = [sv.submit(p.start, p.goal) for p in probs]
+            res = _collect(sv, tk)
+            assert all(res[t]["resid"] < 1e-2 * 1.001 for t in tk)
+            iters[sched] = sum(res[t]["iters"] for t in tk)
+        finally:
+            sv.close()
+    assert iters[True] < 0.75 * iters[False], iters
 
 
 def test_memory_budget_sets_slots_and_queues():
