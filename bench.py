@@ -79,7 +79,7 @@ def serving_problem(n, problem_seed):
     import workloads as W
     key = (n, problem_seed % SERVE_POOL)
     if key not in _serve_pool:
-        _serve_pool[key] = W.config5_problem(n, key[1] + 7919 * n)
+        _serve_pool[key] = W.serving_box(n, key[1] + 7919 * n)
     return _serve_pool[key]
 
 
@@ -98,7 +98,7 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400, rho_schedule=
     from paper_2011_04240_b300 import serving as SV
     prec = PRECISIONS[precision]
     arr = []
-    for t, n, ps in W.config5_schedule(rate, seconds, seed, SERVE_SIZES):
+    for t, n, ps in W.poisson_schedule(rate, seconds, seed, SERVE_SIZES):
         p = serving_problem(n, ps)
         arr.append((t, p.start, p.goal))
     warm = [W.random_box(n, 99991 + n, box=(8.0, 8.0, 4.0)) for n in SERVE_SIZES]
@@ -164,7 +164,7 @@ def job_throughput(units_per_rank, world, ms_max):
 
 def workload(args, rank):
     import workloads as W
-    probs = W.config4(args.batch, seed=rank, n=args.agents)
+    probs = W.shell_batch(args.batch, seed=rank, n=args.agents)
     return probs
 
 
@@ -347,7 +347,7 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4), rho_schedule=None):
     lat, its, res = [], [], []
     for rep in range(2):
         for sd in seeds:
-            p = W.config2(sd)
+            p = W.box16(sd)
             s = torch.from_numpy(p.start[None]).cuda()
             g = torch.from_numpy(p.goal[None]).cuda()
             torch.cuda.synchronize()
@@ -381,7 +381,7 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
     import torch
     import workloads as W
     from paper_2011_04240_b300 import Mixed, Planner, amto
-    probs = W.config3(n_instances, seed=0, sizes=sizes)
+    probs = W.mixed_boxes(n_instances, seed=0, sizes=sizes)
     by_n = {n: [p for p in probs if p.n == n] for n in sizes}
     groups = [by_n[n] for n in sizes if by_n[n]]
     pls = [Planner(gr[0].n, 100, 8.0, proj_mode=amto.PROJ_LITERAL, precision=PRECISIONS[prec],
@@ -607,7 +607,7 @@ def planar_compare(B=256, n=32, K=40):
                         "literal projection, TF32X3 apply", "unit": UNIT, **out}
 
 
-def config1_latency(reps=5):
+def circle4_latency(reps=5):
     """4 agents on a 3 m circle, antipodal goals, m = 50, T = 5 s, 200 fixed
     iterations, literal projection, batch 1: wall time of one solve on the
     device (setup, 200 iterations, FP64 residual) and per iteration."""
@@ -615,7 +615,7 @@ def config1_latency(reps=5):
     import torch
     import workloads as W
     from paper_2011_04240_b300 import Planner
-    p = W.config1()
+    p = W.circle4_swap()
     pl = Planner(4, 50, 5.0, max_batch=1)
     s = torch.from_numpy(p.start[None]).cuda()
     g = torch.from_numpy(p.goal[None]).cuda()
@@ -853,7 +853,7 @@ def main():
             extras["plain_fp32_per_instance"] = plain_per_instance()
             extras["rho_schedule_per_instance"] = plain_per_instance(
                 rho_schedule=(10, 100 ** (1 / 9), 10))
-            extras["config1_latency"] = config1_latency()
+            extras["circle4_latency"] = circle4_latency()
             extras["obstacles"] = obstacle_scaling()
             extras["planar"] = planar_compare()
             extras["serving"] = serving_compare(1000.0, 2.0, args.precision,

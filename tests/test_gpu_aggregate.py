@@ -62,7 +62,7 @@ def test_automatic_choice_and_rejections():
 
 
 @pytest.mark.parametrize("prob,k,precision", [
-    (W.config4(1)[0], 1, "fp32"), (W.config4(1)[0], 3, "fp32"),
+    (W.shell_batch(1)[0], 1, "fp32"), (W.shell_batch(1)[0], 3, "fp32"),
     (W.random_box(33, 23, box=(8.0, 8.0, 4.0), m=41, T=6.0), 30, "fp32"),
     (W.random_box(16, 21, box=(6.0, 6.0, 3.0)), 60, "fp32"),
     (W.random_box(24, 5, box=(8.0, 8.0, 4.0), m=57, T=6.0), 25, "tf32x3"),
@@ -180,7 +180,7 @@ def test_reported_residual_is_the_fp64_maximum(n, B, k):
     """With no per-pair multipliers to read back, recompute f_c of the
     lambda-free reading (Delta min(0, 1 - 1/s)) in FP64 from the returned
     float32 coefficients: its maximum is the reported residual."""
-    probs = W.config4(B) if n == 64 else \
+    probs = W.shell_batch(B) if n == 64 else \
         [W.random_box(n, 910 + i, box=(8.0, 8.0, 4.0)) for i in range(B)]
     pl = planner(probs[0], "R3", max_batch=B)
     x, r, kk = gpu_solve(pl, probs, k)

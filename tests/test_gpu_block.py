@@ -30,7 +30,7 @@ def _planner(prob, B=1, mode="R2", loop=2, G=0, bc_mask=63):
 
 
 @pytest.mark.parametrize("prob,k,mode,G", [
-    (W.config1(), 10, "R2", 0), (W.config1(), 10, "R3", 0),
+    (W.circle4_swap(), 10, "R2", 0), (W.circle4_swap(), 10, "R3", 0),
     (W.random_box(16, 5, box=(6.0, 6.0, 3.0)), 60, "R2", 0),
     (W.random_box(16, 6, box=(6.0, 6.0, 3.0)), 30, "R2", 8),
     (W.random_box(32, 7, box=(8.0, 8.0, 4.0)), 20, "R2", 0),

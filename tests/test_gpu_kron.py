@@ -31,11 +31,11 @@ def _planner(prob, B=1, mode="R2", apply_mode=KRON, loop=1, precision=0):
 
 
 @pytest.mark.parametrize("prob,k,mode,loop", [
-    (W.config1(), 10, "R2", 1), (W.config1(), 10, "R2", 2),
+    (W.circle4_swap(), 10, "R2", 1), (W.circle4_swap(), 10, "R2", 2),
     (W.random_box(16, 21, box=(6.0, 6.0, 3.0)), 50, "R2", 1),
     (W.random_box(16, 22, box=(6.0, 6.0, 3.0)), 50, "R2", 2),
     (W.random_box(33, 23, box=(8.0, 8.0, 4.0), m=41, T=6.0), 20, "R3", 1),
-    (W.config4(1)[0], 1, "R3", 1)])
+    (W.shell_batch(1)[0], 1, "R3", 1)])
 def test_kron_matches_oracle(prob, k, mode, loop):
     from paper_2011_04240_b300 import amto
     pl = _planner(prob, 1, mode, loop=loop)

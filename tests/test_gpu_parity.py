@@ -41,7 +41,7 @@ def test_kkt_inverse_matches_oracle(n, m, T, mask):
     assert pl.info.kkt_check < 1e-7
 
 
-@pytest.mark.parametrize("prob", [W.config1(), W.config2(0), W.random_box(7, 3, m=23, T=3.0)],
+@pytest.mark.parametrize("prob", [W.circle4_swap(), W.box16(0), W.random_box(7, 3, m=23, T=3.0)],
                          ids=["circle4", "box16", "box7_m23"])
 def test_initial_state(prob):
     pl = planner(prob)
@@ -55,7 +55,7 @@ def test_initial_state(prob):
 
 @pytest.mark.parametrize("mode", ["R2", "R3"])
 def test_circle4_within_parity_horizon(mode):
-    prob = W.config1()
+    prob = W.circle4_swap()
     pl = planner(prob, mode)
     M = oracle_mats(prob)
     for k in [1, 2, 5, 10]:
@@ -68,7 +68,7 @@ def test_circle4_within_parity_horizon(mode):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_box16_parity_over_iterations(seed):
-    prob = W.config2(seed)
+    prob = W.box16(seed)
     pl = planner(prob)
     M = oracle_mats(prob)
     for k in [1, 10, 50, 200]:
@@ -80,7 +80,7 @@ def test_box16_parity_over_iterations(seed):
 
 
 def test_box16_tolerance_stop():
-    prob = W.config2(0)
+    prob = W.box16(0)
     pl = planner(prob)
     M = oracle_mats(prob)
     xi, r, k = gpu_solve(pl, [prob], 500, 1e-2)
@@ -136,7 +136,7 @@ def test_batch_matches_single_instances():
 
 
 def test_trace_mode_is_bitwise_identical():
-    prob = W.config2(2)
+    prob = W.box16(2)
     pl = planner(prob)
     xa, ra, ka = gpu_solve(pl, [prob], 30, 1e-3)
     pl.set_trace(True)
@@ -176,7 +176,7 @@ def test_nonfinite_input_is_flagged():
 
 
 def test_shell64_first_iterations():
-    probs = W.config4(2)
+    probs = W.shell_batch(2)
     pl = planner(probs[0], "R3", max_batch=2)
     M = oracle_mats(probs[0])
     xi, r, k = gpu_solve(pl, probs, 1)
@@ -208,7 +208,7 @@ def test_fp64_final_residual_is_the_maximum(n, mode, k, B):
     and lambda^k read back (solves are deterministic), max ||f_c|| =
     max ||lambda^k - lambda^(k-1)|| / rho up to float32 rounding of lambda."""
     if n == 64:
-        probs = W.config4(B)
+        probs = W.shell_batch(B)
     else:
         probs = [W.random_box(n, 900 + i, box=(8.0, 8.0, 4.0)) for i in range(B)]
     pl = planner(probs[0], mode, max_batch=B, multipliers="pairs")

@@ -76,11 +76,11 @@ def test_schedule_on_the_tensor_core_apply(precision, tol):
         assert rel_inf(x[i].reshape(3, -1), st.xi) < tol
 
 
-def test_schedule_batched_config2_shape():
+def test_schedule_batched_16_agent_boxes():
     """16 agents, 6x6x3 m box, the schedule rho 1 -> 100 over ten stages of ten
     solves; a batch of eight through the batched GEMM apply."""
     J, g, E = 10, 100 ** (1 / 9), 10
-    probs = [W.config2(i) for i in range(8)]
+    probs = [W.box16(i) for i in range(8)]
     Ms = _stage_mats(probs[0], J, g)
     pl = _planner(probs[0], J, g, E, B=8, loop=1, apply_mode=1)
     k = 23
@@ -105,7 +105,7 @@ def test_schedule_reaches_the_tolerance_sooner():
     """Sec. IV-A on the GPU: 16 agents in the 6x6x3 m box reach r_max < 1e-2 in
     fewer iterations with rho growing 1 -> 100 than at constant rho = 1, and
     the iteration count agrees with the oracle's."""
-    prob = W.config2(0)
+    prob = W.box16(0)
     J, g, E = 10, 100 ** (1 / 9), 10
     ps = _planner(prob, J, g, E, loop=1)
     pp = _planner(prob, 0, 1.0, 1, loop=1)

@@ -123,7 +123,7 @@ def test_rho_schedule_per_request():
             assert rel_inf(res[t]["xi"].reshape(3, -1), st.xi) < 1e-4
     finally:
         sv.close()
-    probs = [W.config2(i) for i in range(4)]
+    probs = [W.box16(i) for i in range(4)]
     iters = {}
     for sched in (False, True):
         kw = dict(rho_stages=10, rho_growth=100 ** (1 / 9), rho_stage_iters=10) if sched else {}

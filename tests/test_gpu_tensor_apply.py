@@ -26,7 +26,7 @@ def _built():
 
 
 def test_tf32x3_shell64_matches_oracle_and_fp32():
-    probs = W.config4(8)
+    probs = W.shell_batch(8)
     M = oracle_mats(probs[0])
     pt = planner(probs[0], "R3", max_batch=8, precision="tf32x3")
     pf = planner(probs[0], "R3", max_batch=8, precision="fp32")
@@ -59,7 +59,7 @@ def test_tf32x3_partial_tiles_split_k_and_padding(n, m, B):
 
 
 def test_plain_tf32_runs_and_keeps_residual_scale():
-    probs = W.config4(4)
+    probs = W.shell_batch(4)
     pt = planner(probs[0], "R3", max_batch=4, precision="tf32")
     pf = planner(probs[0], "R3", max_batch=4, precision="fp32")
     xt, rt, kt = gpu_solve(pt, probs, 20)
@@ -73,7 +73,7 @@ def test_bf16x3_one_apply_vs_oracle():
     product dropped): one iteration on the 64-agent shell stays within 1e-3
     of the FP64 oracle (measured about 1e-5, since the apply adds an
     increment to xi)."""
-    probs = W.config4(4)
+    probs = W.shell_batch(4)
     M = oracle_mats(probs[0])
     pb = planner(probs[0], "R3", max_batch=4, precision="bf16x3")
     xb, rb, kb = gpu_solve(pb, probs, 1)

@@ -59,7 +59,7 @@ def test_r2_swap_converges():
 
 
 def test_circle4_reaches_paper_residual_level():
-    p = W.config1()
+    p = W.circle4_swap()
     M = O.build_matrices(p.n, p.m, p.degree, p.T, p.a, p.b, p.rho)
     st2 = O.solve(M, p.start, p.goal, 200, 0.0, "R2")
     st3 = O.solve(M, p.start, p.goal, 200, 0.0, "R3")
@@ -71,7 +71,7 @@ def test_circle4_reaches_paper_residual_level():
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_random_box16_reaches_1e2(seed):
-    p = W.config2(seed)
+    p = W.box16(seed)
     M = O.build_matrices(p.n, p.m, p.degree, p.T, p.a, p.b, p.rho)
     st = O.solve(M, p.start, p.goal, 500, 1e-2, "R2")
     assert st.r_max < 1e-2 and st.k < 500
@@ -86,7 +86,7 @@ def test_converged_state_is_fixed_point():
 
 
 def test_direct_and_increment_forms_track():
-    p = W.config2(4)
+    p = W.box16(4)
     M = O.build_matrices(p.n, p.m, p.degree, p.T, p.a, p.b, p.rho)
     a = O.solve(M, p.start, p.goal, 30, 0.0, "R2")
     b = O.solve(M, p.start, p.goal, 30, 0.0, "R2", increment=True)

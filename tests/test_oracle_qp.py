@@ -102,7 +102,7 @@ def test_initial_trajectories_are_straight_segments():
     """With zero end velocities/accelerations the smoothness-only solution is
     the same scalar profile phi(t) on every axis (the problem is linear and
     separable), so each agent moves along the straight start-goal segment."""
-    p = W.config2(3)
+    p = W.box16(3)
     M = O.build_matrices(p.n, p.m, p.degree, p.T, p.a, p.b, p.rho)
     beq = O.boundary_values(p.start, p.goal)
     xi = O.initial_trajectories(M, beq)

@@ -57,7 +57,7 @@ def test_switch_iteration_solves_the_new_stage_qp(mode):
 def test_increasing_rho_reaches_the_tolerance_sooner():
     """Sec. IV-A: the larger penalties of the later iterations speed up the
     loop; 16 agents in a 6x6x3 m box, tol 1e-2."""
-    prob = W.config2(0)
+    prob = W.box16(0)
     hist = []
     plain = O.solve(_mats(prob, 1.0), prob.start, prob.goal, 300, 1e-2)
     g = 100 ** (1 / 9)

@@ -56,7 +56,7 @@ def _regular_solve(pl, prob, iters, tol):
 
 
 def test_static_solve_matches_solve_on_two_calls_in_a_row(lib):
-    probs = [W.config2(0), W.config2(1)]
+    probs = [W.box16(0), W.box16(1)]
     pl = planner(probs[0])
     for prob in probs:  # the second call reuses the array the first one left behind
         xs, rs, ks = _static_solve(lib, pl, prob, 500, 1e-2)

@@ -173,17 +173,17 @@ def obstacle_box(n: int, n_obs: int, seed: int, box=(6.0, 6.0, 3.0), m: int = 10
 # The five workload configurations.
 # ---------------------------------------------------------------------------
 
-def config1() -> Problem:
+def circle4_swap() -> Problem:
     """4 agents, circle of radius 3 m at z = 1 m, antipodal goals, m=50, T=5 s."""
     return circle_swap(4, 3.0, 1.0, m=50, T=5.0)
 
 
-def config2(seed: int = 0) -> Problem:
+def box16(seed: int = 0) -> Problem:
     """16 agents in a 6x6x3 m box, m=100, T=8 s."""
     return random_box(16, seed, box=(6.0, 6.0, 3.0), m=100, T=8.0)
 
 
-def config3(n_instances: int = 512, seed: int = 0, sizes=(8, 16, 24, 32)) -> list[Problem]:
+def mixed_boxes(n_instances: int = 512, seed: int = 0, sizes=(8, 16, 24, 32)) -> list[Problem]:
     """Mixed batch: agent counts uniform in `sizes`, 8x8x4 m box, m=100, T=8 s."""
     rng = np.random.default_rng(seed)
     ns = rng.choice(np.asarray(sizes), size=n_instances)
@@ -191,13 +191,13 @@ def config3(n_instances: int = 512, seed: int = 0, sizes=(8, 16, 24, 32)) -> lis
             for i, n in enumerate(ns)]
 
 
-def config4(n_instances: int = 256, seed: int = 0, n: int = 64) -> list[Problem]:
+def shell_batch(n_instances: int = 256, seed: int = 0, n: int = 64) -> list[Problem]:
     """n agents each on a 5 m sphere shell with antipodal goals, m=100, T=8 s."""
     return [sphere_shell(n, seed * 100003 + i, 5.0, m=100, T=8.0)
             for i in range(n_instances)]
 
 
-def config5_schedule(rate: float, duration_s: float, seed: int = 0,
+def poisson_schedule(rate: float, duration_s: float, seed: int = 0,
                      sizes=(8, 16, 32, 48, 64)):
     """Poisson arrival times with agent counts: list of (t_s, n, problem_seed)."""
     rng = np.random.default_rng(seed)
@@ -214,16 +214,16 @@ def config5_schedule(rate: float, duration_s: float, seed: int = 0,
     return out
 
 
-def config5_problem(n: int, problem_seed: int) -> Problem:
+def serving_box(n: int, problem_seed: int) -> Problem:
     """One serving request: random 8x8x4 m box, m = 100, T = 8 s."""
     return random_box(n, problem_seed, box=(8.0, 8.0, 4.0), m=100, T=8.0)
 
 
-def config5_arrivals(rate: float, duration_s: float, seed: int = 0,
+def poisson_arrivals(rate: float, duration_s: float, seed: int = 0,
                      sizes=(8, 16, 32, 48, 64)):
     """Poisson arrivals: list of (arrival_time_s, Problem) in an 8x8x4 m box."""
-    return [(t, config5_problem(n, ps)) for t, n, ps in
-            config5_schedule(rate, duration_s, seed, sizes)]
+    return [(t, serving_box(n, ps)) for t, n, ps in
+            poisson_schedule(rate, duration_s, seed, sizes)]
 
 
 def stack(problems: list[Problem]):
