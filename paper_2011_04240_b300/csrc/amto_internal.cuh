@@ -39,6 +39,21 @@ __device__ __forceinline__ void griddep_wait() {
 }
 
 
+// Approximate 1/sqrt(x) and x/y with subnormals flushed.  Every call site
+// passes a normal operand (x >= FLT_MIN after a clamp; y a squared unit
+// length), where these give the same values as rsqrtf and __fdividef; they
+// skip the extra instructions that subnormal support costs in the pair loops.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float div_ftz(float x, float y) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+    return r;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args... args) {

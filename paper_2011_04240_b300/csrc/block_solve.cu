@@ -87,7 +87,7 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
     dz = __fmaf_rn(sgb, 1e-18f, dz);  // Delta = 0 -> sigma l_z e_z, as the batched kernel
     const float s2 = __fmaf_rn(__fmul_rn(dz, dz), ib2,
                                __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), ia2));
-    const float is = rsqrtf(fmaxf(s2, FLT_MIN));
+    const float is = rsqrt_ftz(fmaxf(s2, FLT_MIN));
     float fx, fy, fz;
     if (LIT) {
         const float ux = __fmul_rn(dx, is), uy = __fmul_rn(dy, is);
@@ -96,7 +96,7 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
         const float wx = __fmaf_rn(l0, rinv, dx), wy = __fmaf_rn(l1, rinv, dy);
         const float wz = __fmaf_rn(l2, rinv, dz);
         const float wu = __fmaf_rn(wx, ux, __fmaf_rn(wy, uy, __fmul_rn(wz, uz)));
-        const float nd = -fmaxf(1.f, __fdividef(wu, uu));
+        const float nd = -fmaxf(1.f, div_ftz(wu, uu));
         fx = __fmaf_rn(nd, ux, dx);
         fy = __fmaf_rn(nd, uy, dy);
         fz = __fmaf_rn(nd, uz, dz);
