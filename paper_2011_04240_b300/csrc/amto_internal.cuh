@@ -101,6 +101,7 @@ struct Ctl {
     unsigned int active_last;   // instances still iterating after the last pass
     unsigned int error;         // nonzero: a bounded device wait ran out
     int stage;                  // rho stage of the next QP solve (the batch iterates in step)
+    unsigned int unit_next;     // next unit of the pair step to hand out (0 between launches)
 };
 
 // Increasing-rho schedule (Sec. IV-A): rho_j = rho_0 g^j, j < J; QP solve k
