@@ -40,7 +40,7 @@ __device__ __forceinline__ void griddep_wait() {
 
 
 // Approximate 1/sqrt(x) and x/y with subnormals flushed.  Every call site
-// passes a normal operand (x >= FLT_MIN after a clamp; y a squared unit
+// passes a normal operand (x >= FLT_MIN by construction; y a squared unit
 // length), where these give the same values as rsqrtf and __fdividef; they
 // skip the extra instructions that subnormal support costs in the pair loops.
 __device__ __forceinline__ float rsqrt_ftz(float x) {
@@ -51,6 +51,12 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
 __device__ __forceinline__ float div_ftz(float x, float y) {
     float r;
     asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+    return r;
+}
+// max(a, b, c) in one instruction (a NaN operand is ignored, as by fmaxf).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
 

@@ -84,10 +84,10 @@ __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float s
                                            float& l0, float& l1,
                                            float& l2, float& t0, float& t1, float& t2,
                                            float& fsq) {
-    dz = __fmaf_rn(sgb, 1e-18f, dz);  // Delta = 0 -> sigma l_z e_z, as the batched kernel
+    dz = __fmaf_rn(sgb, 1e-12f, dz);  // Delta = 0 -> sigma l_z e_z, as the batched kernel
     const float s2 = __fmaf_rn(__fmul_rn(dz, dz), ib2,
-                               __fmul_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), ia2));
-    const float is = rsqrt_ftz(fmaxf(s2, FLT_MIN));
+                               __fmaf_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), ia2, FLT_MIN));
+    const float is = rsqrt_ftz(s2);
     float fx, fy, fz;
     if (LIT) {
         const float ux = __fmul_rn(dx, is), uy = __fmul_rn(dy, is);
