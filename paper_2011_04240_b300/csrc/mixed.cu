@@ -8,7 +8,7 @@
 //                       (+ k_splitk_reduce_mixed; tensor-core plans launch
 //                       their own apply),
 //   k_pair_mixed        the fused pair step: the (instance, chunk) units of
-//                       all plans strided over one persistent grid, each unit
+//                       all plans handed out to one persistent grid, each unit
 //                       with its plan's geometry,
 // captured once per combination of batch sizes as a CUDA graph under a
 // conditional WHILE node; the last block of k_pair_mixed sets the condition
