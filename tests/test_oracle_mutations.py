@@ -17,6 +17,7 @@ import tests.test_oracle_projection as TP
 import tests.test_oracle_obstacles as TO
 import tests.test_oracle_planar as TPL
 import tests.test_oracle_qp as TQ
+import tests.test_oracle_residual as TR
 
 
 def _fails(fn, *args):
@@ -87,6 +88,18 @@ def _planar_angle_axes_swapped(D, lam, M, mode="R2", a=None, b=None):
     return alpha, np.full_like(alpha, np.pi / 2), OA.d_step(Wd, U), U
 
 
+def _residual_inf_norm(fc):
+    return float(np.abs(fc).max()) if fc.size else 0.0
+
+
+def _residual_rms(fc):
+    return float(np.sqrt(np.mean(np.sum(fc * fc, axis=0)))) if fc.size else 0.0
+
+
+def _residual_squared(fc):
+    return float(np.max(np.sum(fc * fc, axis=0))) if fc.size else 0.0
+
+
 _orig = {k: getattr(OA, k) for k in ["pair_matrix", "alpha_beta", "bernstein_basis",
                                      "obstacle_rows", "obstacle_matrix", "projection"]}
 
@@ -114,6 +127,14 @@ MUTATIONS = {
                                       [(TO.test_single_detour_touches_the_obstacle, "R3", 1.2)]),
     "obstacle rows missing": ("obstacle_matrix", _obstacle_rows_missing_from_gram,
                               [(TO.test_gram_and_inverse_closed_forms, 3, 1, 1.0)]),
+    "residual as largest component": ("residual_max", _residual_inf_norm,
+                                      [(TR.test_residual_max_is_largest_column_euclidean_norm,),
+                                       (TR.test_residual_of_crossing_pair_closed_form, 0.2)]),
+    "residual as RMS": ("residual_max", _residual_rms,
+                        [(TR.test_residual_max_is_largest_column_euclidean_norm,),
+                         (TR.test_residual_of_crossing_pair_closed_form, 0.2)]),
+    "residual squared (no root)": ("residual_max", _residual_squared,
+                                   [(TR.test_residual_of_crossing_pair_closed_form, 0.2)]),
     "planar angle axes swapped": ("projection", _planar_angle_axes_swapped,
                                   [(TPL.test_lambda_free_residual_inside_the_disk,)]),
 }
