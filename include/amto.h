@@ -206,9 +206,12 @@ typedef struct {
  * once and reused for any start/goal).
  *
  * On the current CUDA device: forms the Bernstein basis P, Pdot, Pddot
- * (Eq. param), Q_x, A, A_eq and the KKT matrix of Eq. (kkt_step_x), inverts
- * it by Gauss-Jordan elimination with partial pivoting in FP64, checks
- * max|K K^-1 - I|, and keeps the top block rows of the inverse in float32.
+ * (Eq. param), Q_x, A, A_eq and the KKT matrix of Eq. (kkt_step_x), forms
+ * its inverse in FP64 from the exact agent-level closed form
+ * K^-1 = I (x) K_n^-1 + (1/n) 1 1^T (x) (K_0^-1 - K_n^-1) (two small
+ * agent-level KKT matrices inverted by Gauss-Jordan elimination with partial
+ * pivoting), checks max|K K^-1 - I| against K assembled from its
+ * definition, and keeps the top block rows of the inverse in float32.
  * Allocates all device workspace for `max_batch` instances, so amto_solve
  * allocates nothing.  Synchronous.  Errors: EINVAL for out-of-range
  * params, ENOMEM, ECUDA, ENUMERIC if the inverse fails its self-check.

@@ -3,10 +3,12 @@
 // Forms the Bernstein basis P, Pdot, Pddot (Eq. param), the smoothness
 // Hessian block Pddot^T Pddot, the boundary rows A, the KKT matrix
 //     K = [[Q_x + rho A_fc^T A_fc, A_eq^T], [A_eq, 0]]
-// and its inverse by Gauss-Jordan elimination with partial pivoting, then a
-// self-check max |K K^-1 - I|.  Everything runs in float64 on the device;
-// the host only sequences the launches.  The iteration kernels keep the top
-// n*nv rows of K^-1 in float32.
+// and its inverse from the exact agent-level closed form (two (nv + nb)-square
+// inverses by Gauss-Jordan elimination with partial pivoting, one block each),
+// then a self-check max |K K^-1 - I| against K assembled from its definition.
+// Everything runs in float64 on the device; the host only sequences the
+// launches (about 15 for a constant rho).  The iteration kernels keep the top
+// n*nv rows of K^-1 in float32 (and TF32/BF16 hi/lo copies).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -106,100 +108,91 @@ __global__ void k_assemble(int n, int n_obs, int nv, int nb, double rho, const d
     K[idx] = v;
 }
 
-// Agent-level KKT matrix [[Pddot^T Pddot, A^T], [A, 0]] of the
-// smoothness-only initial solve.
-// Agent-level KKT matrix [[DtD + w PtP, A^T], [A, 0]] (w = 0: smoothness only,
-// the ring of all agents moving together; w = rho n: the block of one agent
-// relative to the others, Remark 1's structure of the full matrix).
-__global__ void k_assemble_agent(int nv, int nb, const double* DtD, const double* PtP, double w,
-                                 const double* A, double* K) {
-    int d = nv + nb;
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= d * d) return;
-    int r = idx / d, c = idx % d;
-    double v = 0.0;
-    if (r < nv && c < nv) v = DtD[r * nv + c] + w * PtP[r * nv + c];
-    else if (r < nv) v = A[(c - nv) * nv + r];
-    else if (c < nv) v = A[(r - nv) * nv + c];
-    K[idx] = v;
-}
+// ---- Agent-level inverses (Remarks 1-2) ------------------------------------
+//
+// With the unknowns of agent i grouped (its nv coefficients, then its nb
+// boundary multipliers), the KKT matrix of Eq. (kkt_step_x) is
+//     K = I (x) K_n - 1 1^T (x) Z,   Z = [[rho P^T P, 0], [0, 0]],
+// K_n = [[Pddot^T Pddot + rho (n + n_obs) P^T P, A^T], [A, 0]]: every pair
+// row of Eq. (A_f) adds rho P^T P to the diagonal blocks of its two agents
+// and -rho P^T P to the two off-diagonal blocks.  With 1 1^T = n Pi (Pi the
+// projector on the agents' mean), K = (I - Pi) (x) K_n + Pi (x) K_0 where
+// K_0 = K_n - n Z carries rho n_obs P^T P (0 without obstacles: the
+// smoothness-only matrix of the initial solve), so
+//     K^-1 = I (x) K_n^-1 + (1/n) 1 1^T (x) (K_0^-1 - K_n^-1)
+// exactly.  Only the two (nv + nb)-square agent-level matrices are inverted.
 
-// ---- Gauss-Jordan with partial pivoting on W = [K | I] (N x 2N) ----------
+constexpr int kMaxAgentDim = 32;  // nv + nb <= 16 + 6
 
-__global__ void k_gj_init(int N, const double* K, double* W) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2LL * N * N) return;
-    int r = (int)(idx / (2 * N)), c = (int)(idx % (2 * N));
-    W[idx] = (c < N) ? K[(long long)r * N + c] : (c - N == r ? 1.0 : 0.0);
-}
-
-// Pivot row p = argmax_{r >= c} |W[r][c]| (ties: smallest r); pv = W[p][c].
-__global__ void k_gj_pivot(int N, int c, const double* W, int* piv, double* pv, int* singular) {
-    __shared__ double sv[1024];
-    __shared__ int si[1024];
-    double best = -1.0;
-    int bi = N;
-    for (int r = c + threadIdx.x; r < N; r += blockDim.x) {
-        double v = fabs(W[(long long)r * 2 * N + c]);
-        if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+// One block per agent-level matrix [[DtD + w PtP, A^T], [A, 0]] (weights w in
+// `wts`): assembled into shared memory as [M | I] and inverted by
+// Gauss-Jordan elimination with partial pivoting (largest |pivot|, ties to
+// the smallest row), FP64.  A zero pivot sets *singular.
+__global__ void k_agent_inverse(int nv, int nb, const double* DtD, const double* PtP,
+                                const double* A, const double* wts, double* inv,
+                                int* singular) {
+    __shared__ double W[kMaxAgentDim][2 * kMaxAgentDim + 1];
+    __shared__ int s_piv;
+    const int d = nv + nb, tid = threadIdx.x, nt = blockDim.x;
+    const double w = wts[blockIdx.x];
+    for (int e = tid; e < d * 2 * d; e += nt) {
+        const int r = e / (2 * d), c = e % (2 * d);
+        double v;
+        if (c >= d) v = (c - d == r) ? 1.0 : 0.0;
+        else if (r < nv && c < nv) v = DtD[r * nv + c] + w * PtP[r * nv + c];
+        else if (r < nv) v = A[(c - nv) * nv + r];
+        else if (c < nv) v = A[(r - nv) * nv + c];
+        else v = 0.0;
+        W[r][c] = v;
     }
-    sv[threadIdx.x] = best;
-    si[threadIdx.x] = bi;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double v2 = sv[threadIdx.x + s];
-            int i2 = si[threadIdx.x + s];
-            if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
-                sv[threadIdx.x] = v2;
-                si[threadIdx.x] = i2;
-            }
+    for (int c = 0; c < d; ++c) {
+        if (tid == 0) {
+            int p = c;
+            double best = fabs(W[c][c]);
+            for (int r = c + 1; r < d; ++r)
+                if (fabs(W[r][c]) > best) { best = fabs(W[r][c]); p = r; }
+            if (!(best > 0.0)) *singular = 1;
+            s_piv = p;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        const double pv = W[p][c];
+        if (!(fabs(pv) > 0.0)) return;  // uniform over the block
+        __syncthreads();
+        for (int j = tid; j < 2 * d; j += nt) {  // swap rows c and p, scale row c
+            const double a = W[c][j], b = W[p][j];
+            if (p != c) W[p][j] = a;
+            W[c][j] = b / pv;
+        }
+        __syncthreads();
+        // eliminate column c from the other rows; column c is read as the
+        // multiplier and left as is (never read again)
+        for (int e = tid; e < d * (2 * d - c - 1); e += nt) {
+            const int r = e / (2 * d - c - 1), j = c + 1 + e % (2 * d - c - 1);
+            if (r == c) continue;
+            const double f = W[r][c];
+            if (f != 0.0) W[r][j] -= f * W[c][j];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        int p = si[0];
-        *piv = p;
-        double v = (p < N) ? W[(long long)p * 2 * N + c] : 0.0;
-        *pv = v;
-        if (!(fabs(v) > 0.0)) *singular = 1;
-    }
+    double* out = inv + (size_t)blockIdx.x * d * d;
+    for (int e = tid; e < d * d; e += nt) out[e] = W[e / d][d + e % d];
 }
 
-// Swap rows c and piv, divide the new row c by the pivot value.
-__global__ void k_gj_swap_scale(int N, int c, double* W, const int* piv, const double* pv) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 2 * N) return;
-    int p = *piv;
-    double v = *pv;
-    if (!(fabs(v) > 0.0) || p >= N) return;
-    double* rc = W + (long long)c * 2 * N;
-    double* rp = W + (long long)p * 2 * N;
-    double a = rc[j], b = rp[j];
-    if (p != c) rp[j] = a;
-    rc[j] = b / v;
-}
-
-// Eliminate column c from every other row.  Only columns j > c of the left
-// half and the whole right half change; column c itself is left as is (it is
-// never read again), so W[r][c] is a stable multiplier during this launch.
-__global__ void k_gj_elim(int N, int c, double* W, const double* pv) {
-    if (!(fabs(*pv) > 0.0)) return;
-    int width = (N - c - 1) + N;
-    int jj = blockIdx.x * blockDim.x + threadIdx.x;
-    int r = blockIdx.y;
-    if (jj >= width || r == c) return;
-    int j = (jj < N - c - 1) ? (c + 1 + jj) : (N + (jj - (N - c - 1)));
-    double* wr = W + (long long)r * 2 * N;
-    double f = wr[c];
-    if (f != 0.0) wr[j] -= f * W[(long long)c * 2 * N + j];
-}
-
-__global__ void k_gj_extract(int N, const double* W, double* Kinv) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)N * N) return;
-    int r = (int)(idx / N), c = (int)(idx % N);
-    Kinv[idx] = W[(long long)r * 2 * N + N + c];
+// Dense K^-1 (kdim x kdim, unknowns [all coefficients ; all multipliers],
+// each agent-major) from the agent-level inverses by the closed form above.
+__global__ void k_kron_inverse(int n, int nv, int nb, const double* Kn_inv, const double* K0_inv,
+                               double* Kinv) {
+    const int d = nv + nb, nvn = n * nv, kdim = n * d;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)kdim * kdim) return;
+    const int r = (int)(idx / kdim), c = (int)(idx % kdim);
+    const int i = r < nvn ? r / nv : (r - nvn) / nb, q = r < nvn ? r % nv : nv + (r - nvn) % nb;
+    const int j = c < nvn ? c / nv : (c - nvn) / nb, q2 = c < nvn ? c % nv : nv + (c - nvn) % nb;
+    const double kn = Kn_inv[q * d + q2];
+    const double mean = (K0_inv[q * d + q2] - kn) / (double)n;
+    Kinv[idx] = i == j ? kn + mean : mean;
 }
 
 // max |K K^-1 - I| as the bits of a non-negative double (atomicMax on the
@@ -271,38 +264,28 @@ inline unsigned blocks(long long count, int threads) {
     return (unsigned)((count + threads - 1) / threads);
 }
 
-// Gauss-Jordan inverse of the N x N device matrix K into Kinv (W: N x 2N).
-amto_status invert(int N, const double* K, double* Kinv, double* W, int* scratch_i,
-                   double* scratch_d, cudaStream_t s) {
-    k_gj_init<<<blocks(2LL * N * N, 256), 256, 0, s>>>(N, K, W);
-    AMTO_CUDA_TRY(cudaMemsetAsync(scratch_i + 1, 0, sizeof(int), s));
-    for (int c = 0; c < N; ++c) {
-        k_gj_pivot<<<1, 1024, 0, s>>>(N, c, W, scratch_i, scratch_d, scratch_i + 1);
-        k_gj_swap_scale<<<blocks(2 * N, 256), 256, 0, s>>>(N, c, W, scratch_i, scratch_d);
-        int width = (N - c - 1) + N;
-        dim3 g(blocks(width, 256), N);
-        k_gj_elim<<<g, 256, 0, s>>>(N, c, W, scratch_d);
-    }
-    k_gj_extract<<<blocks((long long)N * N, 256), 256, 0, s>>>(N, W, Kinv);
-    AMTO_CUDA_TRY(cudaGetLastError());
-    int singular = 0;
-    AMTO_CUDA_TRY(cudaMemcpyAsync(&singular, scratch_i + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AMTO_CUDA_TRY(cudaStreamSynchronize(s));
-    if (singular) {
-        set_error("KKT matrix is singular (zero pivot in Gauss-Jordan elimination)");
-        return AMTO_ENUMERIC;
-    }
-    return AMTO_OK;
-}
-
 }  // namespace
 
 amto_status precompute(amto_plan_s* pl) {
     const int m = pl->m, N = pl->N, nv = pl->nv, nb = pl->nb, n = pl->n, kdim = pl->kdim;
+    const int d = nv + nb, J = pl->sched.J, n_obs = pl->prm.n_obstacles;
     cudaStream_t s = pl->cap_stream;
+    if (d > kMaxAgentDim) {
+        set_error("agent-level KKT block larger than supported");
+        return AMTO_EINVAL;
+    }
+    // agent-level matrices: [0] smoothness only (w = 0); per stage j the
+    // relative block K_n (w = rho_j (n + n_obs)) and, with obstacles, the
+    // common block K_0 (w = rho_j n_obs)
+    const int per_stage = n_obs > 0 ? 2 : 1, nmat = 1 + J * per_stage;
+    double wts[1 + 2 * kMaxRhoStages];
+    wts[0] = 0.0;
+    for (int j = 0; j < J; ++j) {
+        wts[1 + j * per_stage] = pl->sched.rho_d[j] * (n + n_obs);
+        if (n_obs > 0) wts[2 + j * per_stage] = pl->sched.rho_d[j] * n_obs;
+    }
     double *P = nullptr, *dP = nullptr, *ddP = nullptr, *PtP = nullptr, *DtD = nullptr,
-           *A = nullptr, *K = nullptr, *W = nullptr, *K0 = nullptr, *K0inv = nullptr,
-           *Kn = nullptr, *Kninv = nullptr, *Ko = nullptr, *Koinv = nullptr, *sd = nullptr;
+           *A = nullptr, *K = nullptr, *Ainv = nullptr, *dw = nullptr;
     int* si = nullptr;
     unsigned long long* err = nullptr;
     amto_status st = AMTO_OK;
@@ -320,74 +303,44 @@ amto_status precompute(amto_plan_s* pl) {
     PC_ALLOC(DtD, sizeof(double) * nv * nv);
     PC_ALLOC(A, sizeof(double) * nb * nv);
     PC_ALLOC(K, sizeof(double) * (size_t)kdim * kdim);
-    PC_ALLOC(W, sizeof(double) * (size_t)kdim * kdim * 2);
-    PC_ALLOC(K0, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(K0inv, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(Kn, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(Kninv, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(Ko, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(Koinv, sizeof(double) * (nv + nb) * (nv + nb));
-    PC_ALLOC(sd, sizeof(double) * 4);
-    PC_ALLOC(si, sizeof(int) * 4);
-    PC_ALLOC(err, sizeof(unsigned long long));
+    PC_ALLOC(Ainv, sizeof(double) * nmat * d * d);
+    PC_ALLOC(dw, sizeof(double) * nmat);
+    PC_ALLOC(si, sizeof(int));
+    PC_ALLOC(err, sizeof(unsigned long long) * J);
 #undef PC_ALLOC
 
+    if (st == AMTO_OK &&
+        (cudaMemcpyAsync(dw, wts, sizeof(double) * nmat, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemsetAsync(si, 0, sizeof(int), s) != cudaSuccess ||
+         cudaMemsetAsync(err, 0, sizeof(unsigned long long) * J, s) != cudaSuccess)) {
+        cudaGetLastError();
+        set_error("precompute: copy of the agent-level weights failed");
+        st = AMTO_ECUDA;
+    }
     if (st == AMTO_OK) {
         k_basis<<<blocks(m * nv, 128), 128, 0, s>>>(m, N, pl->prm.T, P, dP, ddP);
         k_small<<<blocks(nv * nv, 128), 128, 0, s>>>(m, nv, pl->prm.bc_mask, P, dP, ddP, PtP,
                                                       DtD, A);
-        k_assemble_agent<<<blocks((nv + nb) * (nv + nb), 128), 128, 0, s>>>(nv, nb, DtD, PtP, 0.0,
-                                                                           A, K0);
+        k_agent_inverse<<<nmat, 128, 0, s>>>(nv, nb, DtD, PtP, A, dw, Ainv, si);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("precompute kernel launch failed");
             st = AMTO_ECUDA;
         }
     }
-    if (st == AMTO_OK) st = invert(nv + nb, K0, K0inv, W, si, sd, s);
+    const double* K0inv = Ainv;  // smoothness-only block
     // one cached inverse per rho stage (Remarks 1-2: K depends on rho and n
-    // only); the last one computed, stage 0, stays in Kinv64
-    const int rows = n * nv, d = nv + nb;
-    double worst = 0.0;
-    for (int j = pl->sched.J - 1; j >= 0 && st == AMTO_OK; --j) {
-        const double rho = pl->sched.rho_d[j];
-        const int n_obs = pl->prm.n_obstacles;
-        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, n_obs, nv, nb, rho, PtP,
+    // only); the last one formed, stage 0, stays in Kinv64
+    const int rows = n * nv;
+    for (int j = J - 1; j >= 0 && st == AMTO_OK; --j) {
+        const double* Kninv = Ainv + (size_t)(1 + j * per_stage) * d * d;
+        const double* Kcinv = n_obs > 0 ? Ainv + (size_t)(2 + j * per_stage) * d * d : K0inv;
+        k_kron_inverse<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, nv, nb, Kninv, Kcinv,
+                                                                           pl->Kinv64);
+        // self-check against K assembled directly from its definition
+        k_assemble<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(n, n_obs, nv, nb,
+                                                                       pl->sched.rho_d[j], PtP,
                                                                        DtD, A, K);
-        // agent-level blocks of the structured inverse: the relative motion
-        // sees rho (n + n_obs) P^T P, the common motion rho n_obs P^T P
-        k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * (n + n_obs), A,
-                                                            Kn);
-        if (n_obs > 0)
-            k_assemble_agent<<<blocks(d * d, 128), 128, 0, s>>>(nv, nb, DtD, PtP, rho * n_obs, A,
-                                                                Ko);
-        if (cudaGetLastError() != cudaSuccess) {
-            set_error("precompute kernel launch failed");
-            st = AMTO_ECUDA;
-            break;
-        }
-        st = invert(nv + nb, Kn, Kninv, W, si, sd, s);
-        if (st == AMTO_OK && n_obs > 0) st = invert(nv + nb, Ko, Koinv, W, si, sd, s);
-        if (st == AMTO_OK) st = invert(kdim, K, pl->Kinv64, W, si, sd, s);
-        if (st != AMTO_OK) break;
-        cudaMemsetAsync(err, 0, sizeof(unsigned long long), s);
-        k_check<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(kdim, K, pl->Kinv64, err);
-        unsigned long long bits = 0;
-        cudaMemcpyAsync(&bits, err, sizeof(bits), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) {
-            set_error("precompute self-check failed to run");
-            st = AMTO_ECUDA;
-            break;
-        }
-        double e;
-        memcpy(&e, &bits, sizeof(e));
-        worst = e > worst ? e : worst;
-        if (!(e < 1e-6)) {
-            char buf[160];
-            snprintf(buf, sizeof(buf), "KKT inverse self-check failed: max|K K^-1 - I| = %g", e);
-            set_error(buf);
-            st = AMTO_ENUMERIC;
-            break;
-        }
+        k_check<<<blocks((long long)kdim * kdim, 256), 256, 0, s>>>(kdim, K, pl->Kinv64, err + j);
         // top n*nv rows of the row-major inverse are its first rows*kdim entries
         k_to_f32<<<blocks((long long)rows * kdim, 256), 256, 0, s>>>(
             (long long)rows * kdim, pl->Kinv64, pl->Ktop + j * pl->ks_top);
@@ -401,25 +354,49 @@ amto_status precompute(amto_plan_s* pl) {
                 reinterpret_cast<__nv_bfloat16*>(pl->Kb_hi) + j * pl->ks_bf,
                 reinterpret_cast<__nv_bfloat16*>(pl->Kb_lo) + j * pl->ks_bf);
         k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, Kninv, pl->Kag + j * pl->ks_ag);
-        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, n_obs > 0 ? Koinv : K0inv,
+        k_agent_top<<<blocks(nv * d, 64), 64, 0, s>>>(nv, nb, Kcinv,
                                                       pl->Kag + j * pl->ks_ag + nv * d);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("precompute kernel launch failed");
+            st = AMTO_ECUDA;
+        }
     }
-    pl->kkt_check = worst;
     if (st == AMTO_OK) {
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);
         k_to_f32<<<blocks(nb * nv, 128), 128, 0, s>>>((long long)nb * nv, A, pl->A32);
         cudaMemcpyAsync(pl->P64, P, sizeof(double) * m * nv, cudaMemcpyDeviceToDevice, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-            set_error("precompute extraction failed");
-            st = AMTO_ECUDA;
+    }
+    int singular = 0;
+    unsigned long long bits[kMaxRhoStages] = {};
+    if (st == AMTO_OK &&
+        (cudaMemcpyAsync(&singular, si, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(bits, err, sizeof(unsigned long long) * J, cudaMemcpyDeviceToHost, s) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)) {
+        set_error("precompute failed to run");
+        st = AMTO_ECUDA;
+    }
+    if (st == AMTO_OK && singular) {
+        set_error("KKT matrix is singular (zero pivot in an agent-level inverse)");
+        st = AMTO_ENUMERIC;
+    }
+    double worst = 0.0;
+    for (int j = 0; j < J && st == AMTO_OK; ++j) {
+        double e;
+        memcpy(&e, &bits[j], sizeof(e));
+        worst = e > worst ? e : worst;
+        if (!(e < 1e-6)) {
+            char buf[160];
+            snprintf(buf, sizeof(buf), "KKT inverse self-check failed: max|K K^-1 - I| = %g", e);
+            set_error(buf);
+            st = AMTO_ENUMERIC;
         }
     }
+    pl->kkt_check = worst;
     cudaFree(P); cudaFree(dP); cudaFree(ddP); cudaFree(PtP); cudaFree(DtD); cudaFree(A);
-    cudaFree(K); cudaFree(W); cudaFree(K0); cudaFree(K0inv); cudaFree(Kn); cudaFree(Kninv);
-    cudaFree(Ko); cudaFree(Koinv); cudaFree(sd); cudaFree(si);
-    cudaFree(err);
+    cudaFree(K); cudaFree(Ainv); cudaFree(dw); cudaFree(si); cudaFree(err);
     return st;
 }
 
