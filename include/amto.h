@@ -191,7 +191,9 @@ typedef struct {
                                            right-hand side, apply (+ split-K reduce),
                                            pair step */
     int launches_fixed;                 /* kernels per solve outside the loop: setup,
-                                           initial projection, FP64 residual, outputs */
+                                           initial projection, FP64 residual (two in
+                                           the lambda-free reading: screen and
+                                           confirmation), outputs (+1: block solver) */
     int time_blocks;                    /* pair-kernel time blocks per warp and unit */
     int apply_mode;                     /* AMTO_APPLY_BATCHED, _FUSED or _KRONECKER */
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
@@ -278,19 +280,65 @@ amto_status amto_solve(amto_plan plan, int batch,
  *   start, goal  device [1][n][3] float32;  xi_out device [1][3][n][N+1];
  *   resid_out, iters_out as in amto_solve (device, may be NULL).
  *
- * The first call on a device looks up the array's device address once
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture on the device.  Every call shares the one array
- * and overwrites it; the flags and counters that must start at zero are
- * cleared by each call.  Calls that overlap on the GPU (for example on two
- * streams) race on the array: serialise them.  The loop is driven from the
- * host, which synchronises `stream` every 8 iterations to read the stop
- * flag.  Results are the same as amto_solve on the same plan and inputs.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current) and keeps it for that
+ * device's CUDA context; make that first call before any stream capture on
+ * the device.  A new context on the device (after cudaDeviceReset) is
+ * noticed by its context id and the address looked up again on the next
+ * call.  Every call shares the one array and overwrites it; the flags and
+ * counters that must start at zero are cleared by each call.  Calls that
+ * overlap on the GPU (for example on two streams) race on the array:
+ * serialise them.
+ *
+ * The loop is driven from the host: it launches one iteration's kernels
+ * (right-hand side, the matrix-vector apply, pair step) per pass and
+ * synchronises `stream` every 8 passes to read the stop flag, so up to 7
+ * passes may be launched after every instance has stopped; the device
+ * control block marks the instance done and those passes do no work.
+ * Because it always uses the graph loop's kernels with the one-instance
+ * matrix-vector apply, its trajectories match amto_solve's on the same
+ * plan and inputs within the float32 tolerance of the parity tests (a plan
+ * whose amto_solve runs the batched split-K product or the one-block loop
+ * sums in another order), and near `tol` the iteration count may differ.
  * Errors: EINVAL, ECUDA.
  */
 amto_status amto_solve_static(amto_plan plan, const float* start, const float* goal,
                               int max_iters, float tol, float* xi_out, float* resid_out,
                               int* iters_out, void* stream);
+
+/*
+ * amto_get_aggregate - the multipliers of the last solve on an
+ * AMTO_MULT_AGGREGATE plan, in the form the plan keeps them: A_fc^T lambda
+ * (Eq. A_f's transpose applied to the lambda of Eq. lag_update), the
+ * per-agent, per-coefficient sum of every pair's multiplier times its
+ * basis row with the pair's sign (+ for the first agent of a pair, - for
+ * the second), after the last solve's final update (lambda^K for K
+ * iterations; the warm-start value for K = 0).
+ *
+ *   agg_out  device [batch][3][n][N+1] float32 (written; caller-owned).
+ *
+ * `batch` must equal the last solve's batch.  Asynchronous on `stream`.
+ * Errors: EINVAL (NULL pointers, batch, or a plan that keeps lambda per
+ * pair: read those with amto_get_state).  Together with the returned
+ * trajectories this is the state that amto_solve_from_aggregate resumes from.
+ */
+amto_status amto_get_aggregate(amto_plan plan, int batch, float* agg_out, void* stream);
+
+/*
+ * amto_solve_from_aggregate - amto_solve on an AMTO_MULT_AGGREGATE plan
+ * with warm-start multipliers given in aggregated form: agg_init (device
+ * [batch][3][n][N+1] float32, caller-owned, read before the call's kernels
+ * finish) is A_fc^T lambda, as amto_get_aggregate returns it; it is
+ * equivalent to passing the per-pair lambda it was formed from as
+ * amto_solve's lambda_init.  Every other argument is amto_solve's; xi_init
+ * is usually the trajectories the state was read with.  Errors: EINVAL
+ * (also for a plan that keeps lambda per pair), ECUDA.
+ */
+amto_status amto_solve_from_aggregate(amto_plan plan, int batch, const float* start,
+                                      const float* goal, const float* bc_extra,
+                                      const float* xi_init, const float* agg_init,
+                                      int max_iters, float tol, float* xi_out,
+                                      float* resid_out, int* iters_out, void* stream);
 
 /*
  * amto_get_state - read back the multipliers of the last solve on this plan

@@ -109,6 +109,9 @@ SIGNATURES = {
     "amto_solve_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_float, _P, _P, _P,
                                          _P]),
     "amto_get_state": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "amto_get_aggregate": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "amto_solve_from_aggregate": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P,
+                                                 ctypes.c_int, ctypes.c_float, _P, _P, _P, _P]),
     "amto_set_obstacles": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "amto_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "amto_get_kkt_inverse": (ctypes.c_int, [_P, _P]),
@@ -188,6 +191,17 @@ def solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init, max_iters, t
           xi_out, resid_out, iters_out, stream) -> None:
     _check(load().amto_solve(plan, batch, start, goal, bc_extra, xi_init, lambda_init,
                              max_iters, tol, xi_out, resid_out, iters_out, stream))
+
+
+def solve_from_aggregate(plan, batch, start, goal, bc_extra, xi_init, agg_init, max_iters, tol,
+                         xi_out, resid_out, iters_out, stream) -> None:
+    _check(load().amto_solve_from_aggregate(plan, batch, start, goal, bc_extra, xi_init,
+                                            agg_init, max_iters, tol, xi_out, resid_out,
+                                            iters_out, stream))
+
+
+def get_aggregate(plan, batch, agg_out, stream) -> None:
+    _check(load().amto_get_aggregate(plan, batch, agg_out, stream))
 
 
 def solve_static(plan, start, goal, max_iters, tol, xi_out, resid_out, iters_out,
@@ -324,6 +338,38 @@ class Planner:
               _ptr(iters), self._stream(stream))
         self.last_batch = B
         return xi, resid, iters
+
+    def solve_from_aggregate(self, start, goal, agg_init, max_iters: int, tol: float = 0.0,
+                             bc_extra=None, xi_init=None, out=None, stream=None):
+        """amto_solve with warm-start multipliers A_fc^T lambda [B,3,n,nv]
+        (aggregated plans); returns (xi, resid, iters)."""
+        torch = self._torch
+        B = start.shape[0]
+        n, nv = self.n, self.nv
+        self._check_tensor(start, (B, n, 3), "start")
+        self._check_tensor(goal, (B, n, 3), "goal")
+        self._check_tensor(bc_extra, (B, n, 2, 2, 3), "bc_extra")
+        self._check_tensor(xi_init, (B, 3, n, nv), "xi_init")
+        self._check_tensor(agg_init, (B, 3, n, nv), "agg_init")
+        if out is None:
+            xi = torch.empty((B, 3, n, nv), device=self.device, dtype=torch.float32)
+            resid = torch.empty((B,), device=self.device, dtype=torch.float32)
+            iters = torch.empty((B,), device=self.device, dtype=torch.int32)
+        else:
+            xi, resid, iters = out
+        solve_from_aggregate(self.plan, B, _ptr(start), _ptr(goal), _ptr(bc_extra),
+                             _ptr(xi_init), _ptr(agg_init), int(max_iters), float(tol), _ptr(xi),
+                             _ptr(resid), _ptr(iters), self._stream(stream))
+        self.last_batch = B
+        return xi, resid, iters
+
+    def aggregate(self, stream=None):
+        """A_fc^T lambda [B,3,n,nv] of the last solve (aggregated plans)."""
+        torch = self._torch
+        out = torch.empty((self.last_batch, 3, self.n, self.nv), device=self.device,
+                          dtype=torch.float32)
+        get_aggregate(self.plan, self.last_batch, _ptr(out), self._stream(stream))
+        return out
 
     def set_obstacles(self, obstacles, stream=None):
         """Static obstacles [B, n_obstacles, 5] (centre x, y, z, l_xy, l_z of the

@@ -60,6 +60,13 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
+// min(a, b, c) in one instruction (a NaN operand is ignored, as by fminf).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args... args) {
@@ -90,6 +97,12 @@ inline cudaError_t launch_pdl_c(const void* fn, dim3 grid, dim3 block, size_t sm
     cfg.numAttrs = 1;
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
+
+// Final-residual screen records (lambda-free reading, final_resid.cu): per
+// unit its screened maximum, candidate count, overflow flag, one unused
+// float, then kFinCand (value, code) pairs.
+constexpr int kFinCand = 62;
+constexpr int kFinRecFloats = 4 + 2 * kFinCand;
 
 // Flags per instance (device int).
 enum : int { FLAG_DONE = 1, FLAG_APPLY = 2, FLAG_NONFINITE = 4 };
@@ -207,7 +220,14 @@ struct amto_plan_s {
     float* obst = nullptr;     // [B][n_obs][5] obstacle centres and semi-axes (amto_set_obstacles)
     int obst_batch = 0;        // instances whose obstacles have been set
     float* gpart = nullptr;    // [B][n_chunks][3][n nv]
-    float* rpart = nullptr;    // [B][n_chunks]
+    float* rpart = nullptr;    // [B][n_chunks] max ||f_c||^2 of each pair-kernel unit (float32)
+    float* spart = nullptr;    // [B][n_chunks] min s^2 of each unit (lambda-free reading)
+    float* P32lo = nullptr;    // [m][nv] float32(P64 - P32): P64 as a float pair (final residual)
+    float* fin = nullptr;      // [B][fin_ns][kFinRecFloats] final-residual screen records
+    int* fin_work = nullptr;   // [B fin_ns] final-residual screening chunks to do
+    unsigned* fin_ctl = nullptr;  // [2] chunks listed / taken (cleared by each final residual)
+    float* fin_olim = nullptr; // [B] the final screen's outside-test limit per instance
+    int fin_grid = 0;          // persistent blocks of the final screen
     float* rhs = nullptr;      // [B][3][kp] (TF32-rounded in tensor-core modes)
     float* rhs_lo = nullptr;   // [B][3][kp] residual rhs - rhs (TF32X3 mode)
     unsigned short* rb_hi = nullptr;  // [B][3][kp8] BF16(rhs) (BF16 modes)
@@ -299,6 +319,18 @@ int launches_per_iteration(const amto_plan_s* pl, int batch);
 amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s);
 amto_status launch_final(amto_plan_s* pl, int batch, float* xi_out, float* resid_out,
                          int* iters_out, cudaStream_t s, const int* list = nullptr, int nlist = 0);
+// final_resid.cu: FP64 final residual of the lambda-free reading (unit skip,
+// float-pair screen, FP64 confirmation of the candidates).
+size_t final_free_smem(const amto_plan_s* pl);
+// Screening chunks per instance of the final residual (lambda-free reading).
+int final_free_ns(const PairGeom& g, int n, int m);
+amto_status configure_final_free(amto_plan_s* pl);
+amto_status launch_final_free(amto_plan_s* pl, int batch, cudaStream_t s, const int* list,
+                              int nlist);
+// Aggregated multipliers A_fc^T lambda of the last solve (user axes) / a
+// warm start's into the plan (AGGREGATE plans).
+amto_status launch_lagg_get(amto_plan_s* pl, int batch, float* out, cudaStream_t s);
+amto_status launch_lagg_set(amto_plan_s* pl, int batch, const float* in, cudaStream_t s);
 amto_status launch_state(amto_plan_s* pl, int batch, float* lambda_out, float* alpha_out,
                          float* beta_out, float* d_out, cudaStream_t s);
 }  // namespace amto

@@ -54,7 +54,7 @@ void free_plan(amto_plan_s* pl) {
     }
     pl->graphs.clear();
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kag, pl->Kinv64, pl->Ktop,
-                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->obst, pl->gpart, pl->rpart, pl->rhs,
+                    pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->obst, pl->gpart, pl->rpart, pl->spart, pl->P32lo, pl->fin, pl->fin_work, pl->fin_ctl, pl->fin_olim, pl->rhs,
                     pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
                     pl->gemm_tk, pl->ctl, pl->l2_flush};
@@ -243,6 +243,57 @@ amto_status validate_params(const amto_params& p) {
     return AMTO_OK;
 }
 
+// The solve of amto_solve / amto_solve_from_aggregate (warm-start multipliers
+// per pair in lambda_init, or aggregated in agg_init, at most one of them).
+amto_status solve_impl(amto_plan plan, int batch, const float* start, const float* goal,
+                       const float* bc_extra, const float* xi_init, const float* lambda_init,
+                       const float* agg_init, int max_iters, float tol, float* xi_out,
+                       float* resid_out, int* iters_out, void* stream) {
+    if (!plan) return einval("plan is NULL");
+    if (batch < 1 || batch > plan->prm.max_batch) return einval("batch must be in [1, max_batch]");
+    if (!start || !goal || !xi_out) return einval("start, goal and xi_out are required");
+    if (max_iters < 0) return einval("max_iters must be >= 0");
+    if (!(tol >= 0.f) || !std::isfinite(tol)) return einval("tol must be a finite value >= 0");
+    if (plan->prm.n_obstacles > 0 && batch > plan->obst_batch)
+        return einval("the obstacles of this batch's instances have not been set (amto_set_obstacles)");
+    DeviceGuard g(plan->device);
+    if (!g.ok) {
+        set_error("cannot select the plan's device");
+        return AMTO_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    amto_status st = launch_setup(plan, batch, start, goal, bc_extra, xi_init, max_iters, tol, s);
+    if (st != AMTO_OK) return st;
+    if (plan->agg && lambda_init) st = launch_lambda_aggregate(plan, batch, lambda_init, s);
+    if (st == AMTO_OK && agg_init) st = launch_lagg_set(plan, batch, agg_init, s);
+    if (st != AMTO_OK) return st;
+    st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, 0, 0, s);
+    if (st != AMTO_OK) return st;
+    if (plan->block) {
+        amto_plan_s* one[1] = {plan};
+        st = launch_block_solver(one, &batch, 1, s);
+    } else if (plan->trace) {
+        for (int k = 0; k < KSTAT_N; ++k) {
+            plan->stat_ms[k] = 0.0;
+            plan->stat_cnt[k] = 0;
+        }
+        st = run_traced(plan, batch, max_iters, s);
+    } else {
+        auto it = plan->graphs.find(batch);
+        if (it == plan->graphs.end()) {
+            Graph gr;
+            st = build_graph(plan, batch, gr);
+            if (st != AMTO_OK) return st;
+            it = plan->graphs.emplace(batch, gr).first;
+        }
+        AMTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+    }
+    if (st != AMTO_OK) return st;
+    st = launch_final(plan, batch, xi_out, resid_out, iters_out, s);
+    plan->last_batch = batch;
+    return st;
+}
+
 }  // namespace amto
 
 using namespace amto;
@@ -350,6 +401,15 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     ALLOC(pl->gpart, (size_t)B * pl->geo.n_chunks * 3 * nvn);
     ALLOC(pl->rpart, (size_t)B * pl->geo.n_chunks);
+    ALLOC(pl->spart, (size_t)B * pl->geo.n_chunks);
+    ALLOC(pl->P32lo, (size_t)pl->m * nv);
+    {
+        const size_t ns = (size_t)final_free_ns(pl->geo, pl->n, pl->m);
+        ALLOC(pl->fin, (size_t)B * ns * kFinRecFloats);
+        ALLOC(pl->fin_work, (size_t)B * ns);
+    }
+    ALLOC(pl->fin_ctl, (size_t)2);
+    ALLOC(pl->fin_olim, (size_t)B);
     ALLOC(pl->rhs, (size_t)B * 3 * pl->kp);
     ALLOC(pl->rmax, (size_t)B);
     ALLOC(pl->r64, (size_t)B);
@@ -365,6 +425,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->gemm_tk, (size_t)tiles);
 #undef ALLOC
     if (st == AMTO_OK && (cudaMemset(pl->gemm_tk, 0, sizeof(unsigned) * tiles) != cudaSuccess ||
+                          cudaMemset(pl->fin_ctl, 0, sizeof(unsigned) * 2) != cudaSuccess ||
                           cudaMemset(pl->uticket, 0, sizeof(unsigned) * B) != cudaSuccess)) {
         set_error("cudaMemset failed");
         st = AMTO_ECUDA;
@@ -407,49 +468,38 @@ amto_status amto_solve(amto_plan plan, int batch, const float* start, const floa
                        int max_iters, float tol, float* xi_out, float* resid_out,
                        int* iters_out, void* stream) {
     clear_error();
-    if (!plan) return einval("plan is NULL");
-    if (batch < 1 || batch > plan->prm.max_batch) return einval("batch must be in [1, max_batch]");
-    if (!start || !goal || !xi_out) return einval("start, goal and xi_out are required");
-    if (max_iters < 0) return einval("max_iters must be >= 0");
-    if (!(tol >= 0.f) || !std::isfinite(tol)) return einval("tol must be a finite value >= 0");
-    if (plan->prm.n_obstacles > 0 && batch > plan->obst_batch)
-        return einval("the obstacles of this batch's instances have not been set (amto_set_obstacles)");
-    DeviceGuard g(plan->device);
-    if (!g.ok) {
-        set_error("cannot select the plan's device");
-        return AMTO_ECUDA;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    amto_status st = launch_setup(plan, batch, start, goal, bc_extra, xi_init, max_iters, tol, s);
-    if (st != AMTO_OK) return st;
-    if (plan->agg && lambda_init) st = launch_lambda_aggregate(plan, batch, lambda_init, s);
-    if (st != AMTO_OK) return st;
-    st = launch_pair(plan, batch, lambda_init ? 2 : 1, lambda_init, 0, 0, s);
-    if (st != AMTO_OK) return st;
-    if (plan->block) {
-        amto_plan_s* one[1] = {plan};
-        st = launch_block_solver(one, &batch, 1, s);
-    } else if (plan->trace) {
-        for (int k = 0; k < KSTAT_N; ++k) {
-            plan->stat_ms[k] = 0.0;
-            plan->stat_cnt[k] = 0;
-        }
-        st = run_traced(plan, batch, max_iters, s);
-    } else {
-        auto it = plan->graphs.find(batch);
-        if (it == plan->graphs.end()) {
-            Graph gr;
-            st = build_graph(plan, batch, gr);
-            if (st != AMTO_OK) return st;
-            it = plan->graphs.emplace(batch, gr).first;
-        }
-        AMTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
-    }
-    if (st != AMTO_OK) return st;
-    st = launch_final(plan, batch, xi_out, resid_out, iters_out, s);
-    plan->last_batch = batch;
-    return st;
+    return solve_impl(plan, batch, start, goal, bc_extra, xi_init, lambda_init, nullptr,
+                      max_iters, tol, xi_out, resid_out, iters_out, stream);
 }
+
+amto_status amto_solve_from_aggregate(amto_plan plan, int batch, const float* start,
+                                      const float* goal, const float* bc_extra,
+                                      const float* xi_init, const float* agg_init,
+                                      int max_iters, float tol, float* xi_out,
+                                      float* resid_out, int* iters_out, void* stream) {
+    clear_error();
+    if (!plan) return einval("plan is NULL");
+    if (!plan->agg)
+        return einval("amto_solve_from_aggregate needs a plan with aggregated multipliers "
+                      "(AMTO_MULT_AGGREGATE); use amto_solve's lambda_init");
+    if (!agg_init) return einval("agg_init is NULL");
+    return solve_impl(plan, batch, start, goal, bc_extra, xi_init, nullptr, agg_init, max_iters,
+                      tol, xi_out, resid_out, iters_out, stream);
+}
+
+amto_status amto_get_aggregate(amto_plan plan, int batch, float* agg_out, void* stream) {
+    clear_error();
+    if (!plan || !agg_out) return einval("plan and agg_out are required");
+    if (!plan->agg)
+        return einval("this plan keeps lambda per pair (AMTO_MULT_PAIRS); read it with "
+                      "amto_get_state");
+    if (batch < 1 || batch != plan->last_batch)
+        return einval("batch must equal the last solve's batch");
+    DeviceGuard g(plan->device);
+    return launch_lagg_get(plan, batch, agg_out, (cudaStream_t)stream);
+}
+
+
 
 amto_status amto_get_state(amto_plan plan, int batch, float* lambda_out, float* alpha_out,
                            float* beta_out, float* d_out, void* stream) {
@@ -513,7 +563,9 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->kkt_check = plan->kkt_check;
     out->device_bytes = plan->bytes;
     out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
-    out->launches_fixed = 4;
+    // setup, initial projection, final residual (the lambda-free reading's is
+    // a screen and a confirmation launch), outputs
+    out->launches_fixed = plan->prm.proj_mode == AMTO_PROJ_LITERAL ? 4 : 5;
     out->time_blocks = plan->geo.QW;
     out->apply_mode = plan->kron ? AMTO_APPLY_KRONECKER
                     : plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
@@ -523,7 +575,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->planar = plan->prm.planar;
     if (plan->block) {
         out->launches_per_iteration = 0;
-        out->launches_fixed = 5;  // setup, initial projection, block solver, residual, outputs
+        out->launches_fixed += 1;  // the block solver
     }
     return AMTO_OK;
 }

@@ -213,6 +213,13 @@ __global__ void k_to_f32(long long count, const double* src, float* dst) {
     if (idx < count) dst[idx] = (float)src[idx];
 }
 
+// The rounding error of k_to_f32: lo = float32(x - float32(x)), so that
+// (hi, lo) carries x to about 2^-48 relative.
+__global__ void k_to_f32_lo(long long count, const double* src, float* lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < count) lo[idx] = (float)(src[idx] - (double)(float)src[idx]);
+}
+
 // Round a float32 to TF32 (10 explicit mantissa bits), to nearest, ties to even.
 __device__ __forceinline__ float tf32_round(float x) {
     unsigned u = __float_as_uint(x);
@@ -364,6 +371,7 @@ amto_status precompute(amto_plan_s* pl) {
     if (st == AMTO_OK) {
         k_extract_e0<<<blocks(nv * nb, 64), 64, 0, s>>>(nv, nb, K0inv, pl->E0);
         k_to_f32<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32);
+        k_to_f32_lo<<<blocks(m * nv, 128), 128, 0, s>>>((long long)m * nv, P, pl->P32lo);
         k_to_f32<<<blocks(nv * nv, 128), 128, 0, s>>>((long long)nv * nv, DtD, pl->Q32);
         k_to_f32<<<blocks(nb * nv, 128), 128, 0, s>>>((long long)nb * nv, A, pl->A32);
         cudaMemcpyAsync(pl->P64, P, sizeof(double) * m * nv, cudaMemcpyDeviceToDevice, s);

@@ -33,16 +33,48 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // context id the address belongs to
 
-// Device address of the scratch array on `dev` (the current device), looked
-// up once per device.
+// Id of the calling thread's current CUDA context (unique for the process's
+// lifetime, so a context made after cudaDeviceReset has a new one); 0 when
+// the driver does not provide it, in which case nothing is cached.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on `dev` (the current device).  It is
+// looked up with cudaGetSymbolAddress on the first call in a context and kept
+// for that context: a device reset makes a new context, whose id differs, and
+// the address is looked up again (the module and its array may have moved).
 amto_status scratch_address(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("amto_solve_static: device ordinal out of range");
         return AMTO_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
@@ -52,6 +84,7 @@ amto_status scratch_address(int dev, unsigned char** out) {
             return AMTO_ECUDA;
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
     return AMTO_OK;
@@ -105,6 +138,12 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     const size_t o_lagg = take(pl.agg ? sizeof(float) * 3 * nvn : 0);
     const size_t o_gpart = take(sizeof(float) * NC * 3 * nvn);
     const size_t o_rpart = take(sizeof(float) * NC);
+    const size_t o_spart = take(sizeof(float) * NC);
+    const size_t NSf = (size_t)final_free_ns(pl.geo, pl.n, pl.m);
+    const size_t o_fin = take(sizeof(float) * NSf * kFinRecFloats);
+    const size_t o_fwork = take(sizeof(int) * NSf);
+    const size_t o_fctl = take(sizeof(unsigned) * 2);
+    const size_t o_folim = take(sizeof(float));
     const size_t o_rhs = take(sizeof(float) * 3 * (size_t)pl.kp);
     const size_t o_rmax = take(sizeof(float));
     const size_t o_r64 = take(sizeof(unsigned long long));
@@ -157,6 +196,13 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     v.Lagg = pl.agg ? reinterpret_cast<float*>(base + o_lagg) : nullptr;
     v.gpart = reinterpret_cast<float*>(base + o_gpart);
     v.rpart = reinterpret_cast<float*>(base + o_rpart);
+    v.spart = reinterpret_cast<float*>(base + o_spart);
+    v.fin = reinterpret_cast<float*>(base + o_fin);
+    v.fin_work = reinterpret_cast<int*>(base + o_fwork);
+    v.fin_ctl = reinterpret_cast<unsigned*>(base + o_fctl);
+    v.fin_olim = reinterpret_cast<float*>(base + o_folim);
+    v.fin_grid = pl.fin_grid;
+    v.P32lo = pl.P32lo;
     v.rhs = reinterpret_cast<float*>(base + o_rhs);
     v.rmax = reinterpret_cast<float*>(base + o_rmax);
     v.r64 = reinterpret_cast<unsigned long long*>(base + o_r64);

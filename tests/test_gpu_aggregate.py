@@ -255,3 +255,98 @@ def test_static_solve():
     xr, rr, kr = gpu_solve(pl, [prob], 30)
     assert int(k[0]) == 30
     assert rel_inf(xi.cpu().numpy(), xr) < XI_TOL
+
+
+def _afc_t(M, lam):
+    """A_fc^T lambda per axis, FP64: (3, n nv)."""
+    p, m = M.n * (M.n - 1) // 2, M.m
+    return np.stack([M.A_fc.T @ np.asarray(lam[a], np.float64).reshape(p * m) for a in range(3)])
+
+
+def test_aggregate_read_back_matches_oracle_multipliers():
+    """amto_get_aggregate returns A_fc^T lambda of Eq. (lag_update): after a
+    warm start from the oracle's state at k = 15 (no iteration) it is that
+    state's A_fc^T lambda, and after 1 and 3 more iterations the oracle's."""
+    prob = W.random_box(16, 71, box=(6.0, 6.0, 3.0))
+    M = oracle_mats(prob)
+    st15 = oracle_solve(M, prob, 15, mode="R3")
+    xi0, lam0 = st15.xi.astype(np.float32), st15.lam.astype(np.float32)
+    ws = O.warm_state(M, xi0.astype(np.float64), lam0.astype(np.float64), "R3")
+    beq = O.boundary_values(prob.start, prob.goal)
+    refs = {0: ws}
+    refs[1] = O.am_iteration(M, ws, beq, "R3")
+    refs[3] = O.am_iteration(M, O.am_iteration(M, refs[1], beq, "R3"), beq, "R3")
+    pl = planner(prob, "R3")
+    assert pl.info.multipliers == _amto().MULT_AGGREGATE
+    p = prob.n * (prob.n - 1) // 2
+    for k, ref in refs.items():
+        gpu_solve(pl, [prob], k, xi_init=xi0.reshape(1, 3, prob.n, -1),
+                  lambda_init=lam0.reshape(1, 3, p, prob.m))
+        agg = pl.aggregate().cpu().numpy()[0].reshape(3, -1)
+        want = _afc_t(M, ref.lam)
+        assert rel_inf(agg, want) < (1e-5 if k == 0 else 1e-4), (k, rel_inf(agg, want))
+
+
+@pytest.mark.parametrize("planar", [0, 1])
+def test_aggregate_round_trip_is_bitwise(planar):
+    """Read (xi, A_fc^T lambda) after a solve and resume from them with no
+    iteration: both come back bit for bit (the resume's initial projection
+    updates no multiplier)."""
+    import torch
+    from paper_2011_04240_b300 import Planner
+    probs = [W.random_box(24, 90 + i, box=(8.0, 8.0, 4.0)) for i in range(3)]
+    p0 = probs[0]
+    pl = Planner(p0.n, p0.m, p0.T, p0.a, p0.b, p0.rho, p0.degree, proj_mode=1, max_batch=3,
+                 planar=planar)
+    assert pl.info.multipliers == _amto().MULT_AGGREGATE
+    s, g = W.stack(probs)
+    s, g = torch.from_numpy(s).cuda(), torch.from_numpy(g).cuda()
+    xi1, r1, k1 = pl.solve(s, g, 9)
+    agg1 = pl.aggregate()
+    xi2, r2, k2 = pl.solve_from_aggregate(s, g, agg1.clone(), 0, xi_init=xi1.clone())
+    agg2 = pl.aggregate()
+    torch.cuda.synchronize()
+    assert torch.equal(xi1, xi2) and torch.equal(agg1, agg2)
+    assert np.all(k2.cpu().numpy() == 0)
+    if planar:
+        assert torch.all(agg1[:, 2] == 0)  # the plane has no z multipliers
+
+
+def test_resume_from_aggregate_equals_lambda_init():
+    """A warm start from A_fc^T lambda (formed here in FP64) follows the same
+    iterates as one from the per-pair lambda it came from."""
+    prob = W.random_box(16, 73, box=(6.0, 6.0, 3.0))
+    M = oracle_mats(prob)
+    st15 = oracle_solve(M, prob, 15, mode="R3")
+    xi0, lam0 = st15.xi.astype(np.float32), st15.lam.astype(np.float32)
+    import torch
+    p = prob.n * (prob.n - 1) // 2
+    pl = planner(prob, "R3")
+    xa, ra, ka = gpu_solve(pl, [prob], 4, xi_init=xi0.reshape(1, 3, prob.n, -1),
+                           lambda_init=lam0.reshape(1, 3, p, prob.m))
+    agg = torch.from_numpy(np.ascontiguousarray(
+        _afc_t(M, lam0).astype(np.float32).reshape(1, 3, prob.n, -1))).cuda()
+    x0 = torch.from_numpy(np.ascontiguousarray(xi0.reshape(1, 3, prob.n, -1))).cuda()
+    s, g = W.stack([prob])
+    xb, rb, kb = pl.solve_from_aggregate(torch.from_numpy(s).cuda(), torch.from_numpy(g).cuda(),
+                                         agg, 4, xi_init=x0)
+    torch.cuda.synchronize()
+    assert int(kb[0]) == int(ka[0]) == 4
+    assert rel_inf(xb.cpu().numpy(), xa) < 1e-5
+    ref = O.solve(M, prob.start, prob.goal, 4, mode="R3",
+                  state=O.warm_state(M, xi0.astype(np.float64), lam0.astype(np.float64), "R3"))
+    assert rel_inf(xb.cpu().numpy()[0].reshape(3, -1), ref.xi) < XI_TOL
+
+
+def test_aggregate_calls_reject_per_pair_plans():
+    import torch
+    amto = _amto()
+    prob = W.random_box(8, 75, box=(6.0, 6.0, 3.0))
+    pp = planner(prob, "R3", multipliers="pairs")
+    gpu_solve(pp, [prob], 2)
+    buf = torch.zeros((1, 3, 8, 11), device="cuda")
+    with pytest.raises(amto.AmtoError):
+        amto.get_aggregate(pp.plan, 1, buf.data_ptr(), None)
+    s, g = W.stack([prob])
+    with pytest.raises(amto.AmtoError):
+        pp.solve_from_aggregate(torch.from_numpy(s).cuda(), torch.from_numpy(g).cuda(), buf, 1)
