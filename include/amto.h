@@ -68,7 +68,17 @@ enum {
     AMTO_PREC_BF16X3 = 2,   /* tensor cores (kind::f16, BF16 operands): BF16 hi and BF16
                                lo parts, 3 products, float32 accumulate (~16 bits) */
     AMTO_PREC_TF32 = 3,     /* tensor cores, TF32 operands, single product */
-    AMTO_PREC_BF16 = 4      /* tensor cores, BF16 operands, single product */
+    AMTO_PREC_BF16 = 4,     /* tensor cores, BF16 operands, single product */
+    /* Per-instance switch: the single product (TF32, or BF16) until the
+     * instance's r_max stalls (it has not fallen below (1 - prec_drop) times
+     * its best value within prec_window iterations), then the hi/lo
+     * correction products as well (hi*lo + lo*hi, kept in a second
+     * accumulator that only the switched instances add).  A tensor-core tile
+     * whose instances have not switched skips the correction products.  The
+     * switch is per instance and permanent for the solve; an instance's
+     * arithmetic does not depend on the other instances of its batch. */
+    AMTO_PREC_TF32_ADAPT = 5,
+    AMTO_PREC_BF16_ADAPT = 6
 };
 
 /* Boundary-condition bits (rows of A in Sec. III-B). */
@@ -126,6 +136,10 @@ typedef struct {
      * goal, boundary extras, warm starts, obstacle centres and l_z) are
      * ignored, and the returned z coefficients and multipliers are 0. */
     int planar;
+    /* AMTO_PREC_*_ADAPT only: the stall test's window in iterations (0: 8)
+     * and relative drop (0: 0.02); ignored by the other precisions. */
+    int prec_window;
+    double prec_drop;
 } amto_params;
 
 /* How the multipliers lambda (Eq. lag_update) are kept between iterations.

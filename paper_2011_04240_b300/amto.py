@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libamto.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENUMERIC, EPENDING = range(8)
 PROJ_LITERAL, PROJ_NOLAMBDA = 0, 1
-PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16 = range(5)
+PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16, PREC_TF32_ADAPT, PREC_BF16_ADAPT = range(7)
 APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED, APPLY_KRONECKER = range(4)
 LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
 MULT_AUTO, MULT_PAIRS, MULT_AGGREGATE = range(3)
@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
                 ("rho_stage_iters", ctypes.c_int), ("multipliers", ctypes.c_int),
-                ("n_obstacles", ctypes.c_int), ("planar", ctypes.c_int)]
+                ("n_obstacles", ctypes.c_int), ("planar", ctypes.c_int),
+                ("prec_window", ctypes.c_int), ("prec_drop", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -276,14 +277,15 @@ class Planner:
                  max_batch: int = 1, tile_group: int = 0, tile_time_blocks: int = 0,
                  apply_mode: int = 0, loop_mode: int = 0, rho_stages: int = 0,
                  rho_growth: float = 1.0, rho_stage_iters: int = 1, multipliers: int = 0,
-                 n_obstacles: int = 0, planar: int = 0):
+                 n_obstacles: int = 0, planar: int = 0, prec_window: int = 0,
+                 prec_drop: float = 0.0):
         import torch
         self._torch = torch
         self.plan = None
         self.params = Params(n_agents, m_steps, poly_degree, T, a, b, rho, bc_mask,
                              proj_mode, precision, max_batch, tile_group, tile_time_blocks,
                              apply_mode, loop_mode, rho_stages, rho_growth, rho_stage_iters,
-                             multipliers, n_obstacles, planar)
+                             multipliers, n_obstacles, planar, prec_window, prec_drop)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.plan = create(self.params)
         self.info = get_info(self.plan)

@@ -28,7 +28,25 @@ void clear_error();
 
 // Apply precisions that run on the tensor cores, and those with BF16 operands.
 inline bool prec_tc(int p) { return p != AMTO_PREC_FP32; }
-inline bool prec_bf16(int p) { return p == AMTO_PREC_BF16X3 || p == AMTO_PREC_BF16; }
+inline bool prec_bf16(int p) {
+    return p == AMTO_PREC_BF16X3 || p == AMTO_PREC_BF16 || p == AMTO_PREC_BF16_ADAPT;
+}
+// Per-instance switch from the single product to the hi/lo correction.
+inline bool prec_adapt(int p) { return p == AMTO_PREC_TF32_ADAPT || p == AMTO_PREC_BF16_ADAPT; }
+// Whether the right-hand side's lo part is formed (x3 modes and the switch).
+inline bool prec_lo(int p) {
+    return p == AMTO_PREC_TF32X3 || p == AMTO_PREC_BF16X3 || prec_adapt(p);
+}
+// Stall test of the switch: defaults of its window and relative drop.
+constexpr int kPrecWindow = 8;
+constexpr float kPrecDrop = 0.02f;
+// Per-instance state of the switch (device, [B] each): switched (0/1), the
+// best r_max so far and the iteration it was reached.
+struct PrecState {
+    int* x3;
+    float* best;
+    int* at;
+};
 
 // Programmatic dependent launch: the loop's kernels are launched so that the
 // next one can be scheduled while the previous one drains; each of them waits
@@ -236,6 +254,9 @@ struct amto_plan_s {
     unsigned long long* r64 = nullptr;  // [B] FP64 final residual^2 bits
     int* iters = nullptr;      // [B]
     int* flags = nullptr;      // [B]
+    int* px3 = nullptr;        // [B] hi/lo correction switched on (AMTO_PREC_*_ADAPT)
+    float* pbest = nullptr;    // [B] best r_max so far (the switch's stall test)
+    int* pat = nullptr;        // [B] iteration of that best value
     unsigned* uticket = nullptr;  // [B] finished pair-kernel units per instance
     float* gemm_ws = nullptr;     // split-K partial products of the SIMT apply
     unsigned* gemm_tk = nullptr;  // per-tile tickets of the split-K reduction

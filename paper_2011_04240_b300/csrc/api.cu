@@ -55,7 +55,7 @@ void free_plan(amto_plan_s* pl) {
     pl->graphs.clear();
     void* ptrs[] = {pl->P32, pl->P64, pl->Q32, pl->A32, pl->E0, pl->Kag, pl->Kinv64, pl->Ktop,
                     pl->xi, pl->beq, pl->lam[0], pl->lam[1], pl->Lagg, pl->obst, pl->gpart, pl->rpart, pl->spart, pl->P32lo, pl->fin, pl->fin_work, pl->fin_ctl, pl->fin_olim, pl->rhs,
-                    pl->rmax, pl->r64, pl->iters, pl->flags, pl->uticket, pl->gemm_ws,
+                    pl->rmax, pl->r64, pl->iters, pl->flags, pl->px3, pl->pbest, pl->pat, pl->uticket, pl->gemm_ws,
                     pl->Kt_hi, pl->Kt_lo, pl->rhs_lo, pl->Kb_hi, pl->Kb_lo, pl->rb_hi, pl->rb_lo,
                     pl->gemm_tk, pl->ctl, pl->l2_flush};
     for (void* p : ptrs)
@@ -187,7 +187,9 @@ amto_status validate_params(const amto_params& p) {
     if (nb >= p.poly_degree + 1) return einval("more boundary conditions than coefficients");
     if (p.proj_mode != AMTO_PROJ_LITERAL && p.proj_mode != AMTO_PROJ_NOLAMBDA)
         return einval("proj_mode");
-    if (p.precision < AMTO_PREC_FP32 || p.precision > AMTO_PREC_BF16)
+    if (p.prec_window < 0 || p.prec_window > 100000 || !(p.prec_drop >= 0.0) || !(p.prec_drop < 1.0))
+        return einval("prec_window must be in [0, 100000] and prec_drop in [0, 1)");
+    if (p.precision < AMTO_PREC_FP32 || p.precision > AMTO_PREC_BF16_ADAPT)
         return einval("precision must be one of AMTO_PREC_*");
     if (p.max_batch < 1 || p.max_batch > 65535) return einval("max_batch must be in [1, 65535]");
     if (p.apply_mode < AMTO_APPLY_AUTO || p.apply_mode > AMTO_APPLY_KRONECKER)
@@ -415,6 +417,9 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->r64, (size_t)B);
     ALLOC(pl->iters, (size_t)B);
     ALLOC(pl->flags, (size_t)B);
+    ALLOC(pl->px3, (size_t)B);
+    ALLOC(pl->pbest, (size_t)B);
+    ALLOC(pl->pat, (size_t)B);
     ALLOC(pl->uticket, (size_t)B);
     ALLOC(pl->ctl, (size_t)1);
     if (st == AMTO_OK) st = configure_kernels(pl);

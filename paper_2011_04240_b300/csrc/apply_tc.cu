@@ -111,10 +111,28 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// 32 columns of the 32 lanes a warp owns, one 32-bit value each.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+        "%26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+          "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+          "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+          "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 }  // namespace
 
 struct TcArgs {
     int M, K, N, kper, splits, x3;
+    int adapt;          // per-instance switch: correction products in a second accumulator
+    const int* px3;     // [B] instances that have switched (adapt)
     float* xi;          // [N][M]
     const int* flags;
     float* ws;          // [splits][N][M]
@@ -150,11 +168,20 @@ __global__ void __launch_bounds__(128, 1)
     const unsigned full0 = su32(&bars[0]), empty0 = su32(&bars[kTcStages]),
                    done = su32(&bars[2 * kTcStages]);
     unsigned* err = &A.ctl->error;
+    // switch mode: the tile needs the correction products when any of its
+    // columns' instances has switched (uniform over the block)
+    bool corr = A.x3 != 0;
+    if (A.adapt) {
+        const int col = n0 + tid;  // kBN == blockDim.x
+        corr = __syncthreads_or(col < A.N && A.px3[col / 3] != 0) != 0;
+    }
+    const bool two_acc = A.adapt != 0;  // main and correction accumulators
+    const uint32_t tcols = two_acc ? 2 * kBN : kBN;
 
-    if (warp == 0) {  // tensor memory for the 128 x 128 float32 accumulator
+    if (warp == 0) {  // tensor memory for the 128 x 128 float32 accumulator(s)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          su32(&tmem_slot)),
-                     "r"(kBN)
+                     "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -170,7 +197,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const unsigned tx_bytes = (unsigned)((A.x3 ? 4 : 2) * kTileBytes);
+    const uint32_t tmem_c = two_acc ? tmem + (uint32_t)kBN : tmem;  // correction accumulator
+    const unsigned tx_bytes = (unsigned)((corr ? 4 : 2) * kTileBytes);
     bool ok = true;
 
     if (tid == 0) {  // producer
@@ -186,7 +214,7 @@ __global__ void __launch_bounds__(128, 1)
             tc_expect_tx(fb, tx_bytes);
             tma_load_2d(st, &ta_hi, kx, m0, fb);
             tma_load_2d(st + 2 * kTileBytes, &tb_hi, kx, n0, fb);
-            if (A.x3) {
+            if (corr) {
                 tma_load_2d(st + kTileBytes, &ta_lo, kx, m0, fb);
                 tma_load_2d(st + 3 * kTileBytes, &tb_lo, kx, n0, fb);
             }
@@ -206,11 +234,12 @@ __global__ void __launch_bounds__(128, 1)
                 const uint64_t ah = smem_desc(st + kk * 32);
                 const uint64_t bh = smem_desc(st + 2 * kTileBytes + kk * 32);
                 mma_step<BF>(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
-                if (A.x3) {
+                if (corr) {
                     const uint64_t al = smem_desc(st + kTileBytes + kk * 32);
                     const uint64_t bl = smem_desc(st + 3 * kTileBytes + kk * 32);
-                    mma_step<BF>(tmem, ah, bl, 1u);
-                    mma_step<BF>(tmem, al, bh, 1u);
+                    // x3: into the one accumulator; switch: into the second
+                    mma_step<BF>(tmem_c, ah, bl, (two_acc && kb == 0 && kk == 0) ? 0u : 1u);
+                    mma_step<BF>(tmem_c, al, bh, 1u);
                 }
             }
             mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
@@ -242,6 +271,16 @@ __global__ void __launch_bounds__(128, 1)
                   "=r"(v[30]), "=r"(v[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (two_acc && corr) {  // switched columns add the correction accumulator
+                uint32_t w[32];
+                tmem_ld32(tmem_c + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, w);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < N && A.px3[col / 3])
+                        v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+                }
+            }
             if (row < M) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -260,7 +299,7 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols)
                      : "memory");
     // split-K partials are summed in split order by k_splitk_reduce
 }
@@ -363,6 +402,8 @@ amto_status launch_apply_tc(amto_plan_s* pl, int batch, cudaStream_t s) {
     a.K = pl->kdim;
     a.N = 3 * batch;
     a.x3 = pl->prm.precision == AMTO_PREC_TF32X3 || pl->prm.precision == AMTO_PREC_BF16X3;
+    a.adapt = prec_adapt(pl->prm.precision) ? 1 : 0;
+    a.px3 = pl->px3;
     a.xi = pl->xi;
     a.flags = pl->flags;
     a.ws = pl->gemm_ws;

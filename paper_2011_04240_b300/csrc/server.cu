@@ -53,13 +53,17 @@ size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision,
     const bool agg = proj_mode == AMTO_PROJ_NOLAMBDA && !(precision == AMTO_PREC_FP32 && n <= 8);
     b += agg ? 4 * 3 * nvn : 2 * 4 * (size_t)g.lam_floats;
     b += 4 * (size_t)g.n_chunks * 3 * nvn;     // unit partials
-    b += 4 * (size_t)g.n_chunks;
+    b += 2 * 4 * (size_t)g.n_chunks;           // unit maxima and smallest s^2
+    {   // final-residual screening records and work list (lambda-free reading)
+        const size_t ns = (size_t)final_free_ns(g, n, m);
+        b += ns * (4 * (size_t)kFinRecFloats + 4) + 4;
+    }
     const size_t kp8 = (kdim + 7) / 8 * 8;
     b += 4 * 3 * kp;                                            // right-hand side
-    if (precision == AMTO_PREC_TF32X3 || precision == AMTO_PREC_TF32) b += 4 * 3 * kp;
+    if (prec_tc(precision) && !prec_bf16(precision)) b += 4 * 3 * kp;  // TF32 lo part
     if (prec_bf16(precision)) b += 2 * 2 * 3 * kp8;             // BF16 hi / lo copies
     b += 4 * 8 * 3 * nvn;                      // split-K workspace share
-    b += 32;                                   // flags, counters
+    b += 48;                                   // flags, counters, precision switch
     return b;
 }
 

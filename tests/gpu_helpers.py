@@ -18,20 +18,23 @@ def rel_inf(a, b) -> float:
     return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
 
 
-PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4}
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4, "tf32_adapt": 5,
+              "bf16_adapt": 6}
 
 
 MULT = {"auto": 0, "pairs": 1, "aggregate": 2}
 
 
 def planner(prob: W.Problem, mode="R2", max_batch=1, bc_mask=63, precision="fp32",
-            tile_group=0, tile_time_blocks=0, loop_mode=0, multipliers="auto"):
+            tile_group=0, tile_time_blocks=0, loop_mode=0, multipliers="auto",
+            prec_window=0, prec_drop=0.0):
     from paper_2011_04240_b300 import Planner
     return Planner(prob.n, prob.m, prob.T, prob.a, prob.b, prob.rho, prob.degree,
                    bc_mask=bc_mask, proj_mode=MODES[mode], max_batch=max_batch,
                    precision=PRECISIONS[precision], tile_group=tile_group,
                    tile_time_blocks=tile_time_blocks, loop_mode=loop_mode,
-                   multipliers=MULT[multipliers])
+                   multipliers=MULT[multipliers], prec_window=prec_window,
+                   prec_drop=prec_drop)
 
 
 def to_dev(x, dev):
