@@ -29,9 +29,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4}  # AMTO_PREC_*
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16": 4,  # AMTO_PREC_*
+              "tf32_adapt": 5, "bf16_adapt": 6}
+PRECISION_REF = os.path.join(ROOT, "tests", "golden", "precision_shell64.npz")
 METRIC = "instance-iterations/s and p50/p99 solve latency vs plain FP32, same residual"
 UNIT = "instance-iterations/s"
+# serving sweep and uneven batch of the default run
+SWEEP_RATES = (200.0, 1000.0, 3000.0)
+SWEEP_SECONDS = 5.0
+SWEEP_SEQ_CAP = 300
+MIXED_STEPS = 50
 
 
 def parse():
@@ -160,6 +167,21 @@ def job_throughput(units_per_rank, world, ms_max):
     """Whole-job rate: every rank processes its own units (replicas, weak
     scaling); the elapsed time is the slowest rank's."""
     return world * units_per_rank / (ms_max / 1e3)
+
+
+def bench_config(args, world):
+    """The workload the line is quoted on; the reference arm prints the same."""
+    return {"workload": f"{args.batch} x {args.agents}-agent sphere-shell antipodal swap per "
+                        "GPU, degree-10 Bernstein, m=100, T=8 s, a=0.6, b=1.2, rho=1, "
+                        "lambda-free projection, fixed iterations",
+            "batch_per_gpu": args.batch, "agents": args.agents, "m": 100,
+            "apply_precision": args.precision,
+            "multipliers": "per pair" if args.multipliers == "pairs"
+                           else "aggregated (A_fc^T lambda)",
+            "l2": "L2 flushed (256 MiB write) before the timed solve; the per-iteration state "
+                  "stays in L2 across the solve's iterations when it fits (working_set_mb); "
+                  "cold_l2 times every iteration from HBM",
+            "parallelism": f"replicas x{world}"}
 
 
 def workload(args, rank):
@@ -371,7 +393,8 @@ def plain_per_instance(seeds=(0, 1, 2, 3, 4), rho_schedule=None):
             "iterations": its, "final_resid_max": max(res)}
 
 
-def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_group=0):
+def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_group=0,
+                steps=None):
     """Uneven batch: `n_instances` random 8x8x4 m boxes with agent counts drawn
     uniformly from `sizes` (degree 10, m = 100, T = 8 s, literal projection),
     K fixed iterations.  Timed three ways on device-resident inputs: one mixed
@@ -391,7 +414,7 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
         s_np, g_np = W.stack(gr)
         starts.append(torch.from_numpy(s_np).cuda())
         goals.append(torch.from_numpy(g_np).cuda())
-    K, Wm = args.steps, max(args.warmup, 3)
+    K, Wm = steps or args.steps, max(args.warmup, 3)
     stream = torch.cuda.current_stream()
     # the branch layout (per-count chains overlapping in one graph)
     mxb = Mixed(pls, amto.MIXED_BRANCHES)
@@ -472,65 +495,80 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
     return out
 
 
-def precision_report(args, ks=(1, 2, 5, 10, 20, 200), samples=(0, 85, 170, 255)):
-    """xi error (max|xi - xi_oracle| / max|xi_oracle|) of each apply precision
-    on sampled instances of the batched workload, against the FP64 oracle
-    run on the same inputs, plus the oracle's own sensitivity horizon K_par
-    (largest k at which runs from inputs perturbed by 1e-7 relative noise
-    stay within 1e-4 of the unperturbed run) and the final max residual of
-    every precision at the last k."""
+def _sig(x, d=3):
+    """x rounded to d significant digits (compact JSON)."""
+    if x is None:
+        return None
+    return float(f"{x:.{d}g}")
+
+
+def headline_summary(ex):
+    """The serving sweep, the uneven batch and the precision report in a few
+    hundred bytes, placed last on the JSON line so that a reader of its tail
+    sees them (the full records are earlier on the line)."""
+    out = {}
+    if "serving" in ex:
+        out["serving"] = [
+            {"rate": r["rate_req_s"], "s": r["window_s"],
+             "srv_p50_ms": _sig(r["server"]["p50_ms"]), "srv_p99_ms": _sig(r["server"]["p99_ms"]),
+             "srv_ii_s": _sig(r["server"]["inst_iter_per_s"]),
+             "srv_res": _sig(r["server"]["resid_max"], 2),
+             "fp32_p50_ms": _sig(r["plain_fp32_per_instance"]["p50_ms"]),
+             "fp32_p99_ms": _sig(r["plain_fp32_per_instance"]["p99_ms"]),
+             "fp32_ii_s": _sig(r["plain_fp32_per_instance"]["inst_iter_per_s"]),
+             "fp32_res": _sig(r["plain_fp32_per_instance"]["resid_max"], 2)}
+            for r in ex["serving"]]
+    if "mixed" in ex:
+        mx = ex["mixed"]
+        out["mixed_ii_s"] = {k: _sig(mx[k]["value"]) for k in
+                             ("mixed", "mixed_branches", "per_count_sequential",
+                              "per_count_concurrent_streams")}
+    if "precision" in ex:
+        pr = ex["precision"]
+        out["precision"] = {"k": pr["k"], "K_par": min(pr["oracle_K_par"]),
+                            "xi_err": {p: [_sig(e, 2) for e in v.values()]
+                                       for p, v in pr["errors"].items()},
+                            "res200": {p: _sig(v, 2) for p, v in pr["final_resid_max"].items()}}
+    return out
+
+
+def precision_report(args, probs=None):
+    """xi error max|xi - xi_oracle| / max|xi_oracle| of every apply precision
+    on 4 sampled instances of the 256 x 64-agent shell batch at
+    k in {1, 2, 5, 10, 20, 200}, against the FP64 oracle's iterates stored
+    in tests/golden/precision_shell64.npz (written by the script beside it,
+    which runs only the oracle).  The file also holds each sample's
+    sensitivity horizon K_par: past it, runs of the FP64 oracle itself from
+    inputs perturbed by 1e-7 differ by more than 1e-4, so errors at k > K_par
+    are the problem's chaos, not the arithmetic.  The final max residual of
+    every precision at k = 200 is reported beside the errors."""
     import numpy as np
     import torch
-    import oracle as O
     import workloads as W
     from paper_2011_04240_b300 import Planner, amto
-    probs = workload(args, 0)
-    B, n = len(probs), probs[0].n
-    samples = [i for i in samples if i < B]
-    M = O.build_matrices(n, probs[0].m, probs[0].degree, probs[0].T, probs[0].a, probs[0].b,
-                         probs[0].rho)
-
-    def oracle_run(start, goal, kmax):
-        beq = O.boundary_values(start, goal)
-        st = O.init_state(M, beq, "R3")
-        snaps = {}
-        for k in range(1, kmax + 1):
-            st = O.am_iteration(M, st, beq, "R3")
-            if k in ks:
-                snaps[k] = st.xi.copy()
-        return snaps
-
-    t0 = time.perf_counter()
-    ref = {i: oracle_run(probs[i].start, probs[i].goal, max(ks)) for i in samples}
-    # sensitivity horizon of the problem itself, on the first sample
-    rng = np.random.default_rng(7)
-    p0 = probs[samples[0]]
-    kpar = max(ks)
-    for _ in range(3):
-        ps = (p0.start.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(p0.start.shape)))
-        pg = (p0.goal.astype(np.float64) * (1 + 1e-7 * rng.standard_normal(p0.goal.shape)))
-        pert = oracle_run(ps, pg, max(ks))
-        for k in ks:
-            a, b = pert[k], ref[samples[0]][k]
-            if np.abs(a - b).max() / np.abs(b).max() > 1e-4:
-                kpar = min(kpar, [kk for kk in ks if kk < k][-1] if k > ks[0] else 0)
-                break
-    oracle_s = time.perf_counter() - t0
+    z = np.load(PRECISION_REF)
+    ks = [int(k) for k in z["ks"]]
+    samples = [int(i) for i in z["samples"]]
+    if probs is None or len(probs) != 256 or probs[0].n != 64:
+        probs = W.shell_batch(256, seed=0, n=64)
+    B, n, p0 = len(probs), probs[0].n, probs[0]
     s_np, g_np = W.stack(probs)
     s = torch.from_numpy(s_np).cuda()
     g = torch.from_numpy(g_np).cuda()
     out = {"workload": f"{B} x {n}-agent sphere shell, lambda-free projection",
-           "samples": samples, "k": list(ks), "oracle_K_par": kpar,
-           "oracle_seconds": oracle_s, "errors": {}, "final_resid_max": {}}
+           "samples": samples, "k": ks, "oracle_K_par": [int(k) for k in z["k_par"]],
+           "oracle_final_resid": [float(r) for r in z["r_max_final"]],
+           "errors": {}, "final_resid_max": {}}
     for name, prec in PRECISIONS.items():
-        pl = Planner(n, probs[0].m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho,
-                     probs[0].degree, proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
+        pl = Planner(n, p0.m, p0.T, p0.a, p0.b, p0.rho, p0.degree,
+                     proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B)
         errs = {}
         for k in ks:
             xi, r, it = pl.solve(s, g, k)
-            x = xi.cpu().numpy()
-            errs[k] = max(float(np.abs(x[i].reshape(3, -1) - ref[i][k]).max()
-                                / np.abs(ref[i][k]).max()) for i in samples)
+            x = xi[samples].cpu().numpy()
+            errs[str(k)] = float(max(
+                np.abs(x[j].reshape(3, -1) - z[f"xi_s{i}_k{k}"].reshape(3, -1)).max()
+                / np.abs(z[f"xi_s{i}_k{k}"]).max() for j, i in enumerate(samples)))
             if k == max(ks):
                 out["final_resid_max"][name] = float(r.max().item())
         out["errors"][name] = errs
@@ -665,9 +703,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.batch} x {args.agents}-agent sphere-shell swap, "
-                                   "degree 10, m=100, T=8 s, lambda-free projection",
-                       "sample": sample},
+            "config": bench_config(args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -760,6 +796,7 @@ def main():
     ms = e0.elapsed_time(e1)
     iters_done = int(out[2].sum().item())
     assert iters_done == B * K, (iters_done, B * K)
+    assert (pl.info.multipliers == amto.MULT_PAIRS) == (args.multipliers == "pairs")
     ms_max = max_over_ranks(ms, world, "cuda")
     value = job_throughput(B * K, world, ms_max)
 
@@ -842,13 +879,14 @@ def main():
             kp = traced(1, pp, 20)
             alg = algorithmic_pair_bytes(n, m, B)
             ach = alg / (kp[0] / 1e3) / 1e9
-            extras["roofline_pairs_form"] = {
+            extras["roofline"]["pairs_form"] = {
                 "bound": "hbm", "kernel": "k_pair (pair step, per-pair multipliers)",
                 "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "peak_source": src, "traffic": profile_traffic(n, B, "pairs"),
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kp[0],
                 "kernel_ms_per_iteration": {"pair": kp[0], "rhs": kp[1], "apply": kp[2]}}
             pp.close()
+        extras["working_set_mb"] = working_set_mb(pl, B)
         if rank == 0:
             extras["plain_fp32_per_instance"] = plain_per_instance()
             extras["rho_schedule_per_instance"] = plain_per_instance(
@@ -856,28 +894,20 @@ def main():
             extras["circle4_latency"] = circle4_latency()
             extras["obstacles"] = obstacle_scaling()
             extras["planar"] = planar_compare()
-            extras["serving"] = serving_compare(1000.0, 2.0, args.precision,
-                                                rho_schedule=(10, 100 ** (1 / 9), 10))
+            extras["serving"] = [
+                serving_compare(r, SWEEP_SECONDS, args.precision, seq_cap=SWEEP_SEQ_CAP,
+                                rho_schedule=(10, 100 ** (1 / 9), 10) if r == 1000.0 else None)
+                for r in SWEEP_RATES]
+            extras["mixed"] = mixed_batch(args, steps=MIXED_STEPS)
+            extras["precision"] = precision_report(args, probs if world == 1 else None)
             extras["cpu_baseline"] = cpu_baseline_oracle(probs[0])
+            extras["summary"] = headline_summary(extras)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"{B} x {n}-agent sphere-shell antipodal swap per GPU, "
-                                       "degree-10 Bernstein, m=100, T=8 s, a=0.6, b=1.2, rho=1, "
-                                       "lambda-free projection, fixed iterations",
-                           "batch_per_gpu": B, "agents": n, "m": m,
-                           "apply_precision": args.precision,
-                           "multipliers": "aggregated (A_fc^T lambda)"
-                                          if pl.info.multipliers == amto.MULT_AGGREGATE
-                                          else "per pair",
-                           "l2": "L2 flushed (256 MiB write) before the timed solve; "
-                                 f"per-iteration state {working_set_mb(pl, B):.0f} MB "
-                                 "(trajectories, unit partials, multipliers, right-hand "
-                                 "sides, K^-1) stays in L2 across the solve's iterations "
-                                 "when it fits; see cold_l2 for every iteration from HBM",
-                           "parallelism": f"replicas x{world}"},
+                "config": bench_config(args, world),
                 "clocks": clk.summary(),
                 # setup, initial projection, K x (rhs, apply [+ split-K reduce], pair),
                 # FP64 residual, outputs
