@@ -195,8 +195,8 @@ typedef struct {
     int n_agents, m_steps, nv, nb;      /* nv = N+1 coefficients, nb = #BC rows */
     int kkt_dim;                        /* (nv + nb) * n */
     int group;                          /* agents per lane group of the pair kernel */
-    int t_chunk;                        /* time samples per pair-kernel block */
-    int n_chunks;                       /* pair-kernel blocks per instance */
+    int t_chunk;                        /* time samples per pair-kernel work unit */
+    int n_chunks;                       /* pair-kernel work units per instance */
     long long lambda_floats;            /* float32 multiplier slots per instance (one buffer;
                                            0 for AMTO_MULT_AGGREGATE plans) */
     double kkt_check;                   /* max |K K^-1 - I| of the FP64 inverse */
@@ -205,15 +205,18 @@ typedef struct {
                                            right-hand side, apply (+ split-K reduce),
                                            pair step */
     int launches_fixed;                 /* kernels per solve outside the loop: setup,
-                                           initial projection, FP64 residual (two in
-                                           the lambda-free reading: screen and
-                                           confirmation), outputs (+1: block solver) */
+                                           initial projection, FP64 residual (three
+                                           in the lambda-free reading: unit bounds,
+                                           screen, confirmation), outputs (+1: block
+                                           solver) */
     int time_blocks;                    /* pair-kernel time blocks per warp and unit */
     int apply_mode;                     /* AMTO_APPLY_BATCHED, _FUSED or _KRONECKER */
     int loop_mode;                      /* AMTO_LOOP_GRAPH or AMTO_LOOP_BLOCK */
     int multipliers;                    /* AMTO_MULT_PAIRS or AMTO_MULT_AGGREGATE */
     int n_obstacles;                    /* static obstacles per instance */
     int planar;                         /* 1: disks in the x-y plane */
+    int tuned;                          /* 1: tile, apply and loop came from the
+                                           autotuner's cache (see amto_tune) */
 } amto_info;
 
 /*
@@ -437,11 +440,29 @@ typedef struct {
  * synthetic batch of `batch` instances (agents on a ring, antipodal goals),
  * `iters` fixed iterations each: a plan per candidate is created, solved
  * twice (2 and 2 + iters iterations, the difference is the loop time) and
- * destroyed.  Synchronous; uses the current device.  Copy the best entry's
- * four fields into amto_params before amto_create.
+ * destroyed.  Synchronous; uses the current device.  The best entry is kept
+ * in the tuning cache (below), so that later plans of this shape with an
+ * automatic tile use it; its four fields can also be copied into amto_params.
  * Errors: EINVAL (bad params, 1 <= batch <= max_batch, 1 <= iters <= 1e5),
  * ENOMEM, ECUDA. */
 amto_status amto_tune(const amto_params* params, int batch, int iters, amto_tune_result* out);
+
+/* The tuning cache.  amto_tune keeps its best entry in a process-wide cache
+ * under the key (n_agents, m_steps, poly_degree, batch rounded up to a power
+ * of two, precision, proj_mode, multipliers, n_obstacles, planar, rho_stages,
+ * bc_mask); a later entry of the same key replaces the earlier one.
+ * amto_create (and so the mixed batches and the server, which create their
+ * plans through it) takes the cached tile, apply and loop for a plan of the
+ * same key (max_batch rounded up the same way) whose tile_group,
+ * tile_time_blocks, apply_mode and loop_mode are all 0 (automatic), as long as
+ * the choice is valid for its parameters; amto_info.tuned reports it.
+ * save writes one text line per entry ("amto-tune-v1" and 17 fields); load
+ * merges a file written by save into the cache (EINVAL, nothing merged, on an
+ * unreadable file or a malformed line).  Thread-safe. */
+amto_status amto_tune_cache_save(const char* path);
+amto_status amto_tune_cache_load(const char* path);
+void amto_tune_cache_clear(void);
+int amto_tune_cache_size(void);
 
 /* ------------------------------------------------------------------------
  * Mixed batches: instances with different agent counts iterated as one loop.

@@ -59,7 +59,7 @@ class Info(ctypes.Structure):
                 ("launches_fixed", ctypes.c_int), ("time_blocks", ctypes.c_int),
                 ("apply_mode", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("multipliers", ctypes.c_int), ("n_obstacles", ctypes.c_int),
-                ("planar", ctypes.c_int)]
+                ("planar", ctypes.c_int), ("tuned", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -121,6 +121,10 @@ SIGNATURES = {
     "amto_set_trace": (ctypes.c_int, [_P, ctypes.c_int]),
     "amto_tune": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(TuneResult)]),
+    "amto_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "amto_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "amto_tune_cache_clear": (None, []),
+    "amto_tune_cache_size": (ctypes.c_int, []),
     "amto_mixed_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(_P)]),
     "amto_mixed_solve": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P),
@@ -250,6 +254,24 @@ def tune(params: Params, batch: int, iters: int = 20) -> dict:
     ent = [(r.entries[i].tile_group, r.entries[i].tile_time_blocks, r.entries[i].apply_mode,
             r.entries[i].loop_mode, r.entries[i].us_per_iteration) for i in range(r.n_entries)]
     return {"best": ent[r.best][:4], "entries": ent}
+
+
+def tune_cache_save(path: str) -> None:
+    """Write the tuning cache (amto_tune's best entry per shape) to `path`."""
+    _check(load().amto_tune_cache_save(os.fsencode(path)))
+
+
+def tune_cache_load(path: str) -> None:
+    """Merge a file written by tune_cache_save into the tuning cache."""
+    _check(load().amto_tune_cache_load(os.fsencode(path)))
+
+
+def tune_cache_clear() -> None:
+    load().amto_tune_cache_clear()
+
+
+def tune_cache_size() -> int:
+    return int(load().amto_tune_cache_size())
 
 
 def last_error() -> str:

@@ -268,6 +268,7 @@ struct amto_plan_s {
     bool block = false;        // the loop runs in the one-block-per-instance solver
     bool kron = false;         // K^-1 applied in its exact agent-structured form
     bool agg = false;          // multipliers kept as A_fc^T lambda (AMTO_MULT_AGGREGATE)
+    bool tuned = false;        // tile, apply and loop taken from the autotuner's cache
     cudaStream_t cap_stream = nullptr;
     std::map<int, amto::Graph> graphs;
 
@@ -327,6 +328,10 @@ bool loop_block(const amto_params& p);
 // AMTO_MULT_AUTO resolved: the aggregated multipliers where the reading and
 // the loop allow them.
 bool mult_aggregate(const amto_params& p);
+// The autotuner's cached tile, apply and loop for p's shape (tune.cu): true
+// and *out = p with those four fields set when p leaves all four automatic and
+// a cached entry exists.
+bool tune_lookup(const amto_params& p, amto_params* out);
 // L = A_fc^T lambda_init of a warm start (AGGREGATE plans), one block per
 // instance and axis.
 amto_status launch_lambda_aggregate(amto_plan_s* pl, int batch, const float* lambda_init,

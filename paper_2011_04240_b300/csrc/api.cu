@@ -313,8 +313,22 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     if (!prm) return einval("params is NULL");
     amto_params pp = *prm;
     if (pp.planar == 1) pp.b = pp.a;  // disks: the kernels' l_z is l_xy (z unused)
+    if (amto::validate_params(pp) != AMTO_OK) return AMTO_EINVAL;
+    // automatic tile, apply and loop: the autotuner's cached choice for this
+    // shape, where one exists and is valid for these parameters
+    bool tuned = false;
+    {
+        amto_params t;
+        if (amto::tune_lookup(pp, &t)) {
+            if (amto::validate_params(t) == AMTO_OK) {
+                pp = t;
+                tuned = true;
+            } else {
+                clear_error();
+            }
+        }
+    }
     const amto_params& p = pp;
-    if (amto::validate_params(p) != AMTO_OK) return AMTO_EINVAL;
 
     amto_plan_s* pl = new (std::nothrow) amto_plan_s();
     if (!pl) {
@@ -322,6 +336,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
         return AMTO_ENOMEM;
     }
     pl->prm = p;
+    pl->tuned = tuned;
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
         cudaGetLastError();
         delete pl;
@@ -569,8 +584,8 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->device_bytes = plan->bytes;
     out->launches_per_iteration = launches_per_iteration(plan, plan->prm.max_batch);
     // setup, initial projection, final residual (the lambda-free reading's is
-    // a screen and a confirmation launch), outputs
-    out->launches_fixed = plan->prm.proj_mode == AMTO_PROJ_LITERAL ? 4 : 5;
+    // three launches: unit bounds and pair list, screen, confirmation), outputs
+    out->launches_fixed = plan->prm.proj_mode == AMTO_PROJ_LITERAL ? 4 : 6;
     out->time_blocks = plan->geo.QW;
     out->apply_mode = plan->kron ? AMTO_APPLY_KRONECKER
                     : plan->fused ? AMTO_APPLY_FUSED : AMTO_APPLY_BATCHED;
@@ -578,6 +593,7 @@ amto_status amto_get_info(amto_plan plan, amto_info* out) {
     out->multipliers = plan->agg ? AMTO_MULT_AGGREGATE : AMTO_MULT_PAIRS;
     out->n_obstacles = plan->prm.n_obstacles;
     out->planar = plan->prm.planar;
+    out->tuned = plan->tuned ? 1 : 0;
     if (plan->block) {
         out->launches_per_iteration = 0;
         out->launches_fixed += 1;  // the block solver

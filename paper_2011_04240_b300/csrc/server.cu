@@ -19,6 +19,7 @@
 // plan (the batched apply computes every column independently, and all
 // reductions have a fixed order), so a request's result is the same alone
 // and in any mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>

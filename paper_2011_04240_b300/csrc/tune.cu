@@ -10,9 +10,18 @@
 // into the pair kernel), and so is the loop (the graph loop, or one block per
 // instance running the whole loop).  amto_tune measures every candidate that fits on a
 // synthetic batch of the caller's shape and reports them all.
+//
+// The best candidate is also kept in a process-wide cache keyed by the
+// plan's shape (agents, samples, degree, batch rounded up to a power of two,
+// precision, projection reading, multiplier form, obstacles, planar flag, rho
+// stages, boundary rows); amto_create takes the cached choice for a plan of
+// the same key whose tile, apply and loop are all automatic.  The cache can be
+// written to and read from a text file.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "amto_internal.cuh"
@@ -41,6 +50,57 @@ void synthetic_inputs(int n, int batch, std::vector<float>& start, std::vector<f
         }
 }
 
+struct TuneKey {
+    int n, m, degree, bucket, precision, proj_mode, multipliers, n_obs, planar, rho_stages;
+    unsigned bc;
+    bool operator==(const TuneKey& o) const {
+        return n == o.n && m == o.m && degree == o.degree && bucket == o.bucket &&
+               precision == o.precision && proj_mode == o.proj_mode &&
+               multipliers == o.multipliers && n_obs == o.n_obs && planar == o.planar &&
+               rho_stages == o.rho_stages && bc == o.bc;
+    }
+};
+
+struct TuneChoice {
+    TuneKey key;
+    amto_tune_entry best;
+};
+
+std::mutex g_tune_mu;
+std::vector<TuneChoice> g_tune;  // guarded by g_tune_mu
+
+int batch_bucket(int b) {
+    int k = 1;
+    while (k < b) k <<= 1;
+    return k;
+}
+
+TuneKey tune_key(const amto_params& p, int batch) {
+    TuneKey k;
+    k.n = p.n_agents;
+    k.m = p.m_steps;
+    k.degree = p.poly_degree;
+    k.bucket = batch_bucket(batch);
+    k.precision = p.precision;
+    k.proj_mode = p.proj_mode;
+    k.multipliers = p.multipliers;
+    k.n_obs = p.n_obstacles;
+    k.planar = p.planar;
+    k.rho_stages = p.rho_stages > 1 ? p.rho_stages : 1;
+    k.bc = p.bc_mask;
+    return k;
+}
+
+void tune_put(const TuneKey& k, const amto_tune_entry& e) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (TuneChoice& c : g_tune)
+        if (c.key == k) {
+            c.best = e;
+            return;
+        }
+    g_tune.push_back({k, e});
+}
+
 struct DeviceBuffers {
     float *start = nullptr, *goal = nullptr, *xi = nullptr, *resid = nullptr;
     int* iters = nullptr;
@@ -54,9 +114,111 @@ struct DeviceBuffers {
 };
 
 }  // namespace
+
+bool tune_lookup(const amto_params& p, amto_params* out) {
+    if (p.tile_group != 0 || p.tile_time_blocks != 0 || p.apply_mode != AMTO_APPLY_AUTO ||
+        p.loop_mode != AMTO_LOOP_AUTO)
+        return false;
+    const TuneKey k = tune_key(p, p.max_batch);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneChoice& c : g_tune)
+        if (c.key == k) {
+            *out = p;
+            out->tile_group = c.best.tile_group;
+            out->tile_time_blocks = c.best.tile_time_blocks;
+            out->apply_mode = c.best.apply_mode;
+            out->loop_mode = c.best.loop_mode;
+            return true;
+        }
+    return false;
+}
+
 }  // namespace amto
 
 using namespace amto;
+
+extern "C" void amto_tune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+extern "C" int amto_tune_cache_size(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tune.size();
+}
+
+static const char kTuneMagic[] = "amto-tune-v1";
+
+extern "C" amto_status amto_tune_cache_save(const char* path) {
+    clear_error();
+    if (!path) {
+        set_error("invalid argument: path is NULL");
+        return AMTO_EINVAL;
+    }
+    FILE* f = fopen(path, "w");
+    if (!f) {
+        set_error(std::string("cannot open ") + path + " for writing");
+        return AMTO_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneChoice& c : g_tune) {
+        const TuneKey& k = c.key;
+        fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %u %d %d %d %d %.6f\n", kTuneMagic, k.n, k.m,
+                k.degree, k.bucket, k.precision, k.proj_mode, k.multipliers, k.n_obs, k.planar,
+                k.rho_stages, k.bc, c.best.tile_group, c.best.tile_time_blocks, c.best.apply_mode,
+                c.best.loop_mode, c.best.us_per_iteration);
+    }
+    const bool ok = fclose(f) == 0;
+    if (!ok) {
+        set_error(std::string("writing ") + path + " failed");
+        return AMTO_EINVAL;
+    }
+    return AMTO_OK;
+}
+
+extern "C" amto_status amto_tune_cache_load(const char* path) {
+    clear_error();
+    if (!path) {
+        set_error("invalid argument: path is NULL");
+        return AMTO_EINVAL;
+    }
+    FILE* f = fopen(path, "r");
+    if (!f) {
+        set_error(std::string("cannot open ") + path);
+        return AMTO_EINVAL;
+    }
+    std::vector<TuneChoice> in;
+    char line[512];
+    int lineno = 0;
+    amto_status st = AMTO_OK;
+    while (fgets(line, sizeof line, f)) {
+        ++lineno;
+        if (line[0] == '\n' || line[0] == '#') continue;
+        char magic[32] = {0};
+        TuneChoice c{};
+        TuneKey& k = c.key;
+        const int got = sscanf(line, "%31s %d %d %d %d %d %d %d %d %d %d %u %d %d %d %d %lf", magic,
+                               &k.n, &k.m, &k.degree, &k.bucket, &k.precision, &k.proj_mode,
+                               &k.multipliers, &k.n_obs, &k.planar, &k.rho_stages, &k.bc,
+                               &c.best.tile_group, &c.best.tile_time_blocks, &c.best.apply_mode,
+                               &c.best.loop_mode, &c.best.us_per_iteration);
+        const int G = c.best.tile_group, QW = c.best.tile_time_blocks;
+        if (got != 17 || strcmp(magic, kTuneMagic) != 0 || !(G == 8 || G == 16 || G == 32) ||
+            QW < 1 || QW > 8 || c.best.apply_mode < AMTO_APPLY_BATCHED ||
+            c.best.apply_mode > AMTO_APPLY_FUSED || c.best.loop_mode < AMTO_LOOP_GRAPH ||
+            c.best.loop_mode > AMTO_LOOP_BLOCK) {
+            set_error(std::string(path) + ": line " + std::to_string(lineno) +
+                      " is not a tuning entry");
+            st = AMTO_EINVAL;
+            break;
+        }
+        in.push_back(c);
+    }
+    fclose(f);
+    if (st != AMTO_OK) return st;
+    for (const TuneChoice& c : in) tune_put(c.key, c.best);
+    return AMTO_OK;
+}
 
 extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters,
                                  amto_tune_result* out) {
@@ -159,5 +321,6 @@ extern "C" amto_status amto_tune(const amto_params* params, int batch, int iters
         set_error("no tiling fits these parameters");
         st = AMTO_EINVAL;
     }
+    if (st == AMTO_OK) tune_put(tune_key(base, batch), out->entries[out->best]);
     return st;
 }

@@ -54,7 +54,10 @@ def test_tune_measures_candidates():
     from paper_2011_04240_b300 import amto
     prob = W.random_box(16, 1, box=(8.0, 8.0, 4.0))
     p = amto.Params(16, 100, 10, 8.0, 0.6, 1.2, 1.0, 63, 0, 0, 8, 0, 0, 0, 0)
-    res = amto.tune(p, 8, 5)
+    try:
+        res = amto.tune(p, 8, 5)
+    finally:
+        amto.tune_cache_clear()  # later tests create plans of this shape
     assert len(res["entries"]) >= 10
     assert {e[0] for e in res["entries"]} == {8, 16}
     assert {e[2] for e in res["entries"]} == {amto.APPLY_BATCHED, amto.APPLY_FUSED}
@@ -107,3 +110,43 @@ def test_fused_apply_rejected_for_tensor_core_precisions():
     with pytest.raises(AmtoError):
         _planner(W.random_box(8, 1, box=(8.0, 8.0, 4.0)), 2, apply_mode=amto.APPLY_FUSED,
                  precision=amto.PREC_TF32X3)
+
+
+def test_tuned_choice_drives_automatic_plans(tmp_path):
+    """amto_tune keeps its best entry; a later plan of the same shape with an
+    automatic tile, apply and loop takes it (amto_info.tuned), a plan of
+    another batch size or with an explicit tile does not, and the choice
+    survives a save / clear / load round trip.  The tuned plan still matches
+    the automatic one within the float32 tolerance."""
+    from paper_2011_04240_b300 import amto
+    amto.tune_cache_clear()
+    probs = [W.random_box(24, 8100 + i, box=(8.0, 8.0, 4.0)) for i in range(8)]
+    try:
+        p = amto.Params(24, 100, 10, 8.0, 0.6, 1.2, 1.0, 63, 0, 0, 8, 0, 0, 0, 0)
+        res = amto.tune(p, 8, 5)
+        G, QW, mode, loop = res["best"]
+        assert amto.tune_cache_size() == 1
+
+        def check(pl):
+            assert pl.info.tuned == 1 and pl.info.loop_mode == loop
+            if loop == amto.LOOP_GRAPH:
+                assert (pl.info.group, pl.info.time_blocks, pl.info.apply_mode) == (G, QW, mode)
+
+        pt = _planner(probs[0], 8, loop_mode=0)
+        check(pt)
+        # batch 5 rounds up to the same bucket (8); 32 and an explicit tile do not match
+        check(_planner(probs[0], 5, loop_mode=0))
+        assert _planner(probs[0], 32, loop_mode=0).info.tuned == 0
+        assert _planner(probs[0], 8, G=8, QW=1, loop_mode=0).info.tuned == 0
+        f = tmp_path / "tune.txt"
+        amto.tune_cache_save(str(f))
+        amto.tune_cache_clear()
+        pa = _planner(probs[0], 8, loop_mode=0)
+        assert pa.info.tuned == 0
+        amto.tune_cache_load(str(f))
+        check(_planner(probs[0], 8, loop_mode=0))
+        xt, rt, kt = gpu_solve(pt, probs, 10)
+        xa, ra, ka = gpu_solve(pa, probs, 10)
+        assert np.all(kt == 10) and rel_inf(xt, xa) < 1e-5
+    finally:
+        amto.tune_cache_clear()
