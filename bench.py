@@ -237,7 +237,7 @@ def source_hash():
     h = hashlib.sha256()
     h.update(head.encode())
     h.update(m.group(0).encode() if m else b"")
-    for f in ("amto_internal.cuh", "schedule.cuh"):
+    for f in ("amto_internal.cuh", "pair_math.cuh", "schedule.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2011_04240_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = ["api.cu", "iterate.cu", "precompute.cu", "static_solve.cu", "apply_tc.cu", "server.cu", "mixed.cu", "tune.cu", "block_solve.cu", "final_resid.cu"]
-HEADERS = ["amto_internal.cuh", "schedule.cuh", "structured.cuh"]
+HEADERS = ["amto_internal.cuh", "pair_math.cuh", "schedule.cuh", "structured.cuh"]
 OUT = os.path.join(HERE, "libamto.so")
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-shared"]

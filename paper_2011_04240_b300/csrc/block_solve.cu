@@ -22,6 +22,7 @@
 #include <cfloat>
 
 #include "amto_internal.cuh"
+#include "pair_math.cuh"
 #include "schedule.cuh"
 #include "structured.cuh"
 
@@ -75,44 +76,19 @@ struct BlockArgs {
     BlockGroup g[AMTO_MAX_MIXED_GROUPS];
 };
 
-// The batched kernel's pair arithmetic for one sample (lane orientation):
-// projection, d step, f_c, multiplier update, |f_c|^2 and tt = f_c + lambda/rho'
-// (rho' the penalty of the next QP solve).
+// The batched kernel's pair arithmetic for one sample (lane orientation; the
+// float instance of pair_math.cuh's pair_core, so both round alike):
+// projection, d step, f_c, multiplier update, |f_c|^2 and tt = f_c +
+// lambda/rho' (rho' the penalty of the next QP solve).
 template <bool LIT>
 __device__ __forceinline__ void pair_step1(float dx, float dy, float dz, float sgb, float ia2,
                                            float ib2, float rho, float rinv, float rnx,
                                            float& l0, float& l1,
                                            float& l2, float& t0, float& t1, float& t2,
                                            float& fsq) {
-    dz = __fmaf_rn(sgb, 1e-12f, dz);  // Delta = 0 -> sigma l_z e_z, as the batched kernel
-    const float s2 = __fmaf_rn(__fmul_rn(dz, dz), ib2,
-                               __fmaf_rn(__fmaf_rn(dx, dx, __fmul_rn(dy, dy)), ia2, FLT_MIN));
-    const float is = rsqrt_ftz(s2);
-    float fx, fy, fz;
-    if (LIT) {
-        const float ux = __fmul_rn(dx, is), uy = __fmul_rn(dy, is);
-        const float uz = __fmul_rn(dz, is);
-        const float uu = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, __fmul_rn(uz, uz)));
-        const float wx = __fmaf_rn(l0, rinv, dx), wy = __fmaf_rn(l1, rinv, dy);
-        const float wz = __fmaf_rn(l2, rinv, dz);
-        const float wu = __fmaf_rn(wx, ux, __fmaf_rn(wy, uy, __fmul_rn(wz, uz)));
-        const float nd = -fmaxf(1.f, div_ftz(wu, uu));
-        fx = __fmaf_rn(nd, ux, dx);
-        fy = __fmaf_rn(nd, uy, dy);
-        fz = __fmaf_rn(nd, uz, dz);
-    } else {
-        const float k = fminf(0.f, 1.f - is);
-        fx = __fmul_rn(dx, k);
-        fy = __fmul_rn(dy, k);
-        fz = __fmul_rn(dz, k);
-    }
-    l0 = __fmaf_rn(rho, fx, l0);
-    l1 = __fmaf_rn(rho, fy, l1);
-    l2 = __fmaf_rn(rho, fz, l2);
-    fsq = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
-    t0 = __fmaf_rn(l0, rnx, fx);
-    t1 = __fmaf_rn(l1, rnx, fy);
-    t2 = __fmaf_rn(l2, rnx, fz);
+    float s2;
+    pm::pair_core<float, LIT, true, true>(dx, dy, dz, sgb, ia2, ib2, rho, rinv, rnx, l0, l1, l2,
+                                          t0, t1, t2, fsq, s2);
 }
 
 template <bool LIT>

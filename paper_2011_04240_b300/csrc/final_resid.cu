@@ -34,6 +34,7 @@
 #include <cmath>
 
 #include "amto_internal.cuh"
+#include "pair_math.cuh"
 
 namespace amto {
 
@@ -140,24 +141,20 @@ __device__ __forceinline__ float screen_value(const float4& hi, const float4& li
     const float dx = __fadd_rn(__fsub_rn(hi.x, hj.x), __fsub_rn(li.x, lj.x));
     const float dy = __fadd_rn(__fsub_rn(hi.y, hj.y), __fsub_rn(li.y, lj.y));
     const float dz = __fadd_rn(__fsub_rn(hi.z, hj.z), __fsub_rn(li.z, lj.z));
-    const float nrm2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float s2 = fmaf(dz * dz, wz, (dx * dx + dy * dy) * wxy);
+    float dxy, dz2;  // s^2 and its parts as pair_math.cuh forms them (each within ~3 u)
+    const float s2 = pm::spheroid_s2(dx, dy, dz, wxy, wz, 0.f, dxy, dz2);
+    const float nrm2 = pm::vadd(dxy, dz2);
     if (!(nrm2 >= 4.f * FLT_MIN) || !(s2 >= FLT_MIN))  // coincident to float32 range:
         return lz;                                      // u = (0, 0, l_z), reading R-degen
     if (s2 >= 1.f) return 0.f;
     // |Delta| (1/s - 1) with |Delta| = nrm2 / sqrt(nrm2)
-    return nrm2 * rsqrt_ftz(nrm2) * (rsqrt_ftz(s2) - 1.f);
+    return nrm2 * pm::vrsqrt(nrm2) * (pm::vrsqrt(s2) - 1.f);
 }
 
-// FP64 ||f_c||^2 of the lambda-free closed form.
+// FP64 ||f_c||^2 of the lambda-free closed form (pair_math.cuh).
 __device__ __forceinline__ double free_f2_f64(double dx, double dy, double dz, double ia2,
                                               double ib2, double lz) {
-    const double s2 = (dx * dx + dy * dy) * ia2 + dz * dz * ib2;
-    if (s2 == 0.0) return lz * lz;  // reading R-degen
-    if (s2 >= 1.0) return 0.0;
-    const double s = sqrt(s2);
-    const double k = 1.0 / s - 1.0;
-    return (dx * dx + dy * dy + dz * dz) * k * k;
+    return pm::fsq_f64(dx, dy, dz, 0.0, 0.0, 0.0, ia2, ib2, lz, 0.0, 0);
 }
 
 __device__ __forceinline__ double pos64(const FreeArgs& A, int b, int ax, int ag, int t) {
