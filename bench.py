@@ -427,6 +427,17 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
     torch.cuda.synchronize()
     ms_branches = e0.elapsed_time(e1)
     mxb.close()
+    # the loops layout (every count's own loop, parallel branches of one graph)
+    mxl = Mixed(pls, amto.MIXED_LOOPS)
+    outs = mxl.solve(starts, goals, Wm)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(stream)
+    mxl.solve(starts, goals, K, out=outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loops = e0.elapsed_time(e1)
+    mxl.close()
     mx = Mixed(pls, amto.MIXED_FUSED)
     outs = mx.solve(starts, goals, Wm)
     torch.cuda.synchronize()
@@ -481,6 +492,9 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
            "mixed_branches": {"value": n_instances * K / (ms_branches / 1e3),
                               "ms_per_step": ms_branches / K,
                               "layout": "per-count chains as parallel graph branches"},
+           "mixed_loops": {"value": n_instances * K / (ms_loops / 1e3),
+                           "ms_per_step": ms_loops / K,
+                           "layout": "per-count loops as parallel graph branches"},
            "per_count_sequential": {"value": n_instances * K / (ms_seq / 1e3),
                                     "ms_per_step": ms_seq / K},
            "per_count_concurrent_streams": {"value": n_instances * K / (ms_conc / 1e3),
@@ -521,7 +535,7 @@ def headline_summary(ex):
     if "mixed" in ex:
         mx = ex["mixed"]
         out["mixed_ii_s"] = {k: _sig(mx[k]["value"]) for k in
-                             ("mixed", "mixed_branches", "per_count_sequential",
+                             ("mixed", "mixed_branches", "mixed_loops", "per_count_sequential",
                               "per_count_concurrent_streams")}
     if "precision" in ex:
         pr = ex["precision"]

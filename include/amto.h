@@ -487,8 +487,13 @@ int amto_tune_cache_size(void);
  * grouped apply and one persistent pair-step launch over the units of all
  * plans.  BRANCHES: every plan's own chain (right-hand side, apply, pair
  * step) as a parallel branch of the graph body, joined by one kernel that
- * sets the loop condition, so different agent counts overlap on the device. */
-enum { AMTO_MIXED_FUSED = 0, AMTO_MIXED_BRANCHES = 1 };
+ * sets the loop condition, so different agent counts overlap on the device.
+ * LOOPS: every plan's own loop (its own conditional WHILE node over its
+ * chain, its own stopping count) as a parallel branch of one graph, joined
+ * only when all have finished: no count waits for another between
+ * iterations.  With LOOPS each plan's penalty schedule follows its own pass
+ * count, as in its own solve. */
+enum { AMTO_MIXED_FUSED = 0, AMTO_MIXED_BRANCHES = 1, AMTO_MIXED_LOOPS = 2 };
 
 typedef struct amto_mixed_s* amto_mixed;
 

@@ -23,7 +23,7 @@ PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_TF32, PREC_BF16, PREC_TF32_ADAPT, PREC
 APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED, APPLY_KRONECKER = range(4)
 LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
 MULT_AUTO, MULT_PAIRS, MULT_AGGREGATE = range(3)
-MIXED_FUSED, MIXED_BRANCHES = range(2)
+MIXED_FUSED, MIXED_BRANCHES, MIXED_LOOPS = range(3)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
 STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",

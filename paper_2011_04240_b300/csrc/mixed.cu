@@ -19,7 +19,11 @@
 // apply, pair step) as a parallel branch of the graph body, joined by one
 // kernel that sets the loop condition: the chains of different agent counts
 // overlap on the device, so one count's apply runs beside another's pair
-// step.
+// step.  Layout AMTO_MIXED_LOOPS gives every plan its own loop: one graph
+// whose parallel branches are the plans' own conditional WHILE nodes, each
+// over its plan's chain with its plan's handle and control block (the
+// graph of a single-plan solve, side by side), joined at the end; no count
+// waits for another between iterations.
 #include <map>
 #include <new>
 #include <string>
@@ -30,8 +34,8 @@
 struct amto_mixed_s {
     std::vector<amto_plan_s*> pls;
     int layout = AMTO_MIXED_FUSED;
-    std::vector<cudaStream_t> br;      // BRANCHES: one stream per plan
-    std::vector<cudaEvent_t> ev;       // BRANCHES: fork event, then one join event per plan
+    std::vector<cudaStream_t> br;      // one stream per plan (branches; setup and outputs)
+    std::vector<cudaEvent_t> ev;       // fork event, then one join event per plan
     int device = 0;
     int grid = 0;                  // persistent grid of the fused pair kernel
     amto::Ctl* ctl = nullptr;      // loop control (device)
@@ -79,6 +83,40 @@ amto_status build_mixed_graph(amto_mixed_s* mx, const std::vector<int>& batch, G
         if (g.graph) cudaGraphDestroy(g.graph);
         return st;
     };
+    if (mx->layout == AMTO_MIXED_LOOPS) {
+        // a WHILE node per plan, no edges between them: parallel loops
+        const int ng = (int)mx->pls.size();
+        for (int q = 0; q < ng; ++q) {
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, g.graph, 1, cudaGraphCondAssignDefault) !=
+                cudaSuccess)
+                return fail(AMTO_ECUDA, "cudaGraphConditionalHandleCreate failed");
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            if (cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp) != cudaSuccess)
+                return fail(AMTO_ECUDA, "cudaGraphAddNode (while) failed");
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(mx->cap, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return fail(AMTO_ECUDA, "cudaStreamBeginCaptureToGraph failed");
+            amto_plan_s* pl = mx->pls[q];
+            amto_status st = launch_rhs(pl, batch[q], mx->cap);
+            if (st == AMTO_OK) st = launch_apply(pl, batch[q], mx->cap);
+            if (st == AMTO_OK) st = launch_pair(pl, batch[q], 0, nullptr, h, 1, mx->cap);
+            cudaGraph_t captured = body;
+            const cudaError_t ce = cudaStreamEndCapture(mx->cap, &captured);
+            if (st != AMTO_OK) return fail(st, nullptr);
+            if (ce != cudaSuccess)
+                return fail(AMTO_ECUDA, "stream capture of a plan's iteration failed");
+        }
+        if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess)
+            return fail(AMTO_ECUDA, "cudaGraphInstantiate failed");
+        out = g;
+        return AMTO_OK;
+    }
     if (cudaGraphConditionalHandleCreate(&g.handle, g.graph, 1, cudaGraphCondAssignDefault) !=
         cudaSuccess)
         return fail(AMTO_ECUDA, "cudaGraphConditionalHandleCreate failed");
@@ -107,6 +145,26 @@ amto_status build_mixed_graph(amto_mixed_s* mx, const std::vector<int>& batch, G
 // Host-driven loop (profilers cannot see kernels under conditional nodes).
 amto_status run_mixed_traced(amto_mixed_s* mx, const std::vector<int>& batch, int max_iters,
                              cudaStream_t s) {
+    if (mx->layout == AMTO_MIXED_LOOPS) {  // every plan's chain while it has work left
+        const int ng = (int)mx->pls.size();
+        for (int it = 0; it <= max_iters + 1; ++it) {
+            for (int q = 0; q < ng; ++q)
+                AMTO_CUDA_TRY(cudaMemcpyAsync(mx->pls[q]->ctl_host, mx->pls[q]->ctl, sizeof(Ctl),
+                                              cudaMemcpyDeviceToHost, s));
+            AMTO_CUDA_TRY(cudaStreamSynchronize(s));
+            bool any = false;
+            for (int q = 0; q < ng; ++q) {
+                if (mx->pls[q]->ctl_host->active_last == 0) continue;
+                any = true;
+                amto_status st = launch_rhs(mx->pls[q], batch[q], s);
+                if (st == AMTO_OK) st = launch_apply(mx->pls[q], batch[q], s);
+                if (st == AMTO_OK) st = launch_pair(mx->pls[q], batch[q], 0, nullptr, 0, 0, s);
+                if (st != AMTO_OK) return st;
+            }
+            if (!any) break;
+        }
+        return AMTO_OK;
+    }
     for (int it = 0; it <= max_iters + 1; ++it) {
         AMTO_CUDA_TRY(cudaMemcpyAsync(mx->ctl_host, mx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         AMTO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -144,8 +202,10 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, a
         return AMTO_EINVAL;
     }
     *out = nullptr;
-    if (layout != AMTO_MIXED_FUSED && layout != AMTO_MIXED_BRANCHES) {
-        set_error("invalid argument: layout must be AMTO_MIXED_FUSED or AMTO_MIXED_BRANCHES");
+    if (layout != AMTO_MIXED_FUSED && layout != AMTO_MIXED_BRANCHES &&
+        layout != AMTO_MIXED_LOOPS) {
+        set_error("invalid argument: layout must be AMTO_MIXED_FUSED, AMTO_MIXED_BRANCHES or "
+                  "AMTO_MIXED_LOOPS");
         return AMTO_EINVAL;
     }
     if (n_plans < 1 || n_plans > AMTO_MAX_MIXED_GROUPS) {
@@ -208,7 +268,7 @@ amto_status amto_mixed_create(const amto_plan* plans, int n_plans, int layout, a
         st = AMTO_ECUDA;
     }
     if (st == AMTO_OK) st = configure_pair_mixed(mx->pls.data(), n_plans, &mx->grid);
-    for (int g = 0; g <= n_plans && st == AMTO_OK && layout == AMTO_MIXED_BRANCHES; ++g) {
+    for (int g = 0; g <= n_plans && st == AMTO_OK; ++g) {
         cudaEvent_t e = nullptr;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
@@ -272,9 +332,18 @@ amto_status amto_mixed_solve(amto_mixed mx, const int* batch, const float* const
     } restore{prev, mx->device};
     cudaStream_t s = (cudaStream_t)stream;
     amto_status st = launch_ctl_reset(mx->ctl, max_iters, tol, s);
+    if (st != AMTO_OK) return st;
+    // every plan's setup and initial projection on its own stream, in parallel
+    AMTO_CUDA_TRY(cudaEventRecord(mx->ev[0], s));
     for (int g = 0; g < ng && st == AMTO_OK; ++g) {
-        st = launch_setup(mx->pls[g], b[g], start[g], goal[g], nullptr, nullptr, max_iters, tol, s);
-        if (st == AMTO_OK) st = launch_pair(mx->pls[g], b[g], 1, nullptr, 0, 0, s);
+        cudaStream_t bs = mx->br[g];
+        AMTO_CUDA_TRY(cudaStreamWaitEvent(bs, mx->ev[0], 0));
+        st = launch_setup(mx->pls[g], b[g], start[g], goal[g], nullptr, nullptr, max_iters, tol, bs);
+        if (st == AMTO_OK) st = launch_pair(mx->pls[g], b[g], 1, nullptr, 0, 0, bs);
+        if (st == AMTO_OK) {
+            AMTO_CUDA_TRY(cudaEventRecord(mx->ev[1 + g], bs));
+            AMTO_CUDA_TRY(cudaStreamWaitEvent(s, mx->ev[1 + g], 0));
+        }
     }
     if (st != AMTO_OK) return st;
     if (mx->trace) {
@@ -289,10 +358,19 @@ amto_status amto_mixed_solve(amto_mixed mx, const int* batch, const float* const
         }
         AMTO_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
     }
+    if (st != AMTO_OK) return st;
+    // every plan's FP64 final residual and outputs on its own stream, in parallel
+    AMTO_CUDA_TRY(cudaEventRecord(mx->ev[0], s));
     for (int g = 0; g < ng && st == AMTO_OK; ++g) {
+        cudaStream_t bs = mx->br[g];
+        AMTO_CUDA_TRY(cudaStreamWaitEvent(bs, mx->ev[0], 0));
         st = launch_final(mx->pls[g], b[g], xi_out[g], resid_out ? resid_out[g] : nullptr,
-                          iters_out ? iters_out[g] : nullptr, s);
+                          iters_out ? iters_out[g] : nullptr, bs);
         mx->pls[g]->last_batch = b[g];
+        if (st == AMTO_OK) {
+            AMTO_CUDA_TRY(cudaEventRecord(mx->ev[1 + g], bs));
+            AMTO_CUDA_TRY(cudaStreamWaitEvent(s, mx->ev[1 + g], 0));
+        }
     }
     return st;
 }

@@ -51,13 +51,16 @@ def _plan(prob, B, precision="fp32", apply_mode=0):
 
 @pytest.mark.parametrize("precision,apply_mode,layout", [("fp32", 2, 0), ("fp32", 1, 0),
                                                           ("tf32x3", 0, 0), ("fp32", 0, 1),
-                                                          ("tf32x3", 0, 1), ("fp32", 2, 1)])
+                                                          ("tf32x3", 0, 1), ("fp32", 2, 1),
+                                                          ("fp32", 0, 2), ("tf32x3", 0, 2),
+                                                          ("fp32", 2, 2)])
 def test_mixed_matches_per_plan_solves_and_oracle(precision, apply_mode, layout):
     """apply_mode 2: every group applies K^-1 inside the pair kernel (one
     launch per iteration); 1 (and 0 = automatic): grouped right-hand-side and
     GEMM launches (per-group tensor-core GEMMs for tf32x3).  layout 0: one
     fused pair launch over all groups; 1: per-group chains as parallel
-    branches of the graph."""
+    branches of the graph; 2: per-group loops as parallel branches (each
+    group runs its own solve's kernels: bitwise the per-plan solve)."""
     from paper_2011_04240_b300 import Mixed
     sizes, batches = (8, 16, 24, 32, 5), (6, 5, 7, 5, 6)
     groups = _groups(sizes, batches, 11)
@@ -69,12 +72,14 @@ def test_mixed_matches_per_plan_solves_and_oracle(precision, apply_mode, layout)
         assert np.all(k == 10)
         xs, rs, ks = gpu_solve(pls[g], probs, 10)
         assert rel_inf(x, xs) < 1e-6, (sizes[g], rel_inf(x, xs))
+        if layout == 2:
+            assert np.array_equal(x, xs) and np.array_equal(r, rs)
         st = oracle_solve(oracle_mats(probs[0]), probs[0], 10)
         assert rel_inf(x[0].reshape(3, -1), st.xi) < 1e-4
     mx.close()
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_mixed_tolerance_stop_per_instance_and_trace_mode(layout):
     from paper_2011_04240_b300 import Mixed
     sizes, batches = (8, 16, 24, 32), (16, 16, 16, 16)
@@ -90,6 +95,8 @@ def test_mixed_tolerance_stop_per_instance_and_trace_mode(layout):
         assert np.array_equal(x, xt) and np.array_equal(k, kt)
         xs, rs, ks = gpu_solve(pls[g], probs, 500, tol=1e-2)
         assert np.all(np.abs(k - ks) <= 2), (sizes[g], k, ks)
+        if layout == 2:  # each group's own loop: its own solve, stop included
+            assert np.array_equal(k, ks) and np.array_equal(x, xs)
         done = k < 500
         assert np.all(r[done] < 1e-2 * 1.001)  # FP64 recheck of a float32 stop
         assert np.all(r[~done] >= 1e-2 * 0.999)
