@@ -551,10 +551,11 @@ typedef struct {
     float tol;             /* per-request stopping tolerance on max ||f_c|| */
     size_t memory_budget;  /* device bytes for resident per-instance state (xi, multipliers,
                               partial sums, right-hand sides); 0 = half the free memory.
-                              Each agent count gets an equal share; its slot count is
-                              the number of instances whose state fits in it (at most
-                              max_slots).  Each count's cached inverse and the plan's
-                              fixed buffers come on top of the budget. */
+                              Each agent count starts with an equal share (its fair
+                              share): as many slots as instances whose state fits in
+                              it, at most max_slots.  See `admission` for how the
+                              shares then move.  Each count's cached inverse and the
+                              plan's fixed buffers come on top of the budget. */
     /* Increasing rho per request (as amto_params; 0 or 1: constant rho).  The
      * slots are not in step, so each request follows the schedule from its
      * own QP count; the server then applies K^-1 in its structured form
@@ -562,7 +563,25 @@ typedef struct {
     int rho_stages;
     double rho_growth;
     int rho_stage_iters;
+    /* AMTO_ADMIT_SHARED (0, default): one budget for all counts.  Between
+     * chunks, the count with the most queued requests beyond its free slots
+     * doubles its slot capacity (up to max_slots or the whole budget), from
+     * unclaimed budget and by shrinking other counts: an idle count (empty
+     * queue) down to max(min(8, its fair share), the next power of two >= its
+     * resident instances), a count with a queue never below its fair share.
+     * A count grows, and a donor shrinks, by a quarter of its capacity or more.
+     * While a count waits below its fair share, counts above theirs admit no
+     * new requests beyond it.  A resize moves the resident instances' state to
+     * a plan of the new capacity (the cached inverse is taken over, not
+     * recomputed); their results do not change, because every shape choice
+     * (lane group, the apply's split over K) is fixed at creation by the
+     * largest capacity the count can reach.  During a resize the count's old
+     * and new state exist side by side for a moment.
+     * AMTO_ADMIT_FIXED (1): every count keeps its fair share. */
+    int admission;
 } amto_server_params;
+
+enum { AMTO_ADMIT_SHARED = 0, AMTO_ADMIT_FIXED = 1 };
 
 typedef struct {
     int n_agents;          /* must be one of the served counts */
@@ -580,7 +599,11 @@ typedef struct {
 typedef struct {
     long long completed, iterations, chunks;
     int n_groups;
-    int sizes[32], slots[32];
+    int sizes[32], slots[32];  /* served counts and their current slot capacities */
+    int fair_slots[32];        /* each count's fair share of the budget, in slots */
+    int max_capacity[32];      /* the largest capacity each count may reach */
+    long long resizes;         /* capacity changes so far (AMTO_ADMIT_SHARED) */
+    size_t budget, budget_used;  /* the memory budget and the bytes the slots hold */
 } amto_server_stats_t;
 
 /* Create a server and start its worker thread on the current device.

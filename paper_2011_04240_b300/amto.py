@@ -24,6 +24,7 @@ APPLY_AUTO, APPLY_BATCHED, APPLY_FUSED, APPLY_KRONECKER = range(4)
 LOOP_AUTO, LOOP_GRAPH, LOOP_BLOCK = range(3)
 MULT_AUTO, MULT_PAIRS, MULT_AGGREGATE = range(3)
 MIXED_FUSED, MIXED_BRANCHES, MIXED_LOOPS = range(3)
+ADMIT_SHARED, ADMIT_FIXED = range(2)
 BC_POS0, BC_VEL0, BC_ACC0, BC_POST, BC_VELT, BC_ACCT, BC_ALL = 1, 2, 4, 8, 16, 32, 63
 
 STATUS_NAMES = {0: "AMTO_OK", 1: "AMTO_EINVAL", 2: "AMTO_ENOMEM", 3: "AMTO_ECUDA",
@@ -71,7 +72,7 @@ class ServerParams(ctypes.Structure):
                 ("chunk_iters", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("tol", ctypes.c_float), ("memory_budget", ctypes.c_size_t),
                 ("rho_stages", ctypes.c_int), ("rho_growth", ctypes.c_double),
-                ("rho_stage_iters", ctypes.c_int)]
+                ("rho_stage_iters", ctypes.c_int), ("admission", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -88,7 +89,10 @@ class ResultInfo(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
                 ("chunks", ctypes.c_longlong), ("n_groups", ctypes.c_int),
-                ("sizes", ctypes.c_int * 32), ("slots", ctypes.c_int * 32)]
+                ("sizes", ctypes.c_int * 32), ("slots", ctypes.c_int * 32),
+                ("fair_slots", ctypes.c_int * 32), ("max_capacity", ctypes.c_int * 32),
+                ("resizes", ctypes.c_longlong), ("budget", ctypes.c_size_t),
+                ("budget_used", ctypes.c_size_t)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -508,7 +512,7 @@ class Server:
     def __init__(self, sizes, m_steps=100, T=8.0, a=0.6, b=1.2, rho=1.0, poly_degree=10,
                  proj_mode=PROJ_LITERAL, precision=PREC_FP32, max_slots=64, chunk_iters=8,
                  max_iters=2000, tol=1e-2, memory_budget=0, rho_stages=0, rho_growth=1.0,
-                 rho_stage_iters=1):
+                 rho_stage_iters=1, admission=0):
         import numpy as np
         self._np = np
         self.sizes = [int(x) for x in sizes]
@@ -517,7 +521,7 @@ class Server:
         self._sizes_arr = arr
         prm = ServerParams(len(self.sizes), arr, m_steps, poly_degree, T, a, b, rho, proj_mode,
                            precision, max_slots, chunk_iters, max_iters, tol, memory_budget,
-                           rho_stages, rho_growth, rho_stage_iters)
+                           rho_stages, rho_growth, rho_stage_iters, admission)
         h = _P()
         _check(load().amto_server_create(ctypes.byref(prm), ctypes.byref(h)))
         self.handle = h.value
@@ -552,8 +556,12 @@ class Server:
     def stats(self):
         s = ServerStats()
         _check(load().amto_server_stats(self.handle, ctypes.byref(s)))
+        ng = s.n_groups
         return {"completed": s.completed, "iterations": s.iterations, "chunks": s.chunks,
-                "slots": {s.sizes[i]: s.slots[i] for i in range(s.n_groups)}}
+                "slots": {s.sizes[i]: s.slots[i] for i in range(ng)},
+                "fair_slots": {s.sizes[i]: s.fair_slots[i] for i in range(ng)},
+                "max_capacity": {s.sizes[i]: s.max_capacity[i] for i in range(ng)},
+                "resizes": s.resizes, "budget": s.budget, "budget_used": s.budget_used}
 
     def close(self):
         if getattr(self, "handle", None):

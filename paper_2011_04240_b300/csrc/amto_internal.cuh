@@ -208,7 +208,13 @@ struct amto_plan_s {
     int n = 0, m = 0, N = 0, nv = 0, nb = 0, kdim = 0, p = 0;
     amto::PairGeom geo{};
     double kkt_check = 0.0;
-    size_t bytes = 0;
+    size_t bytes = 0;          // device bytes held by the plan
+    size_t bytes_const = 0;    // of which the constants (taken over by a resized plan)
+    // the batch that fixes the shape choices (the pair kernel's lane group,
+    // the apply kernel and its split over K, the block loop): max_batch for
+    // amto_create; a resizable plan's largest capacity, so that an instance's
+    // arithmetic does not depend on the capacity allocated
+    int ref_batch = 0;
 
     // constants (device)
     float* P32 = nullptr;      // [m][nv]
@@ -289,6 +295,19 @@ bool apply_fused(const amto_params& p);
 // Checks of amto_params (no CUDA call); sets the error text on failure.
 amto_status validate_params(const amto_params& p);
 amto_status precompute(amto_plan_s* pl);
+// api.cu: a plan for validated parameters with shape choices of a batch of
+// ref_batch (>= p.max_batch) instances; with a donor of the same parameters,
+// its constants are taken over instead of recomputed (the donor is unchanged
+// on failure).
+amto_status create_plan(const amto_params& p, int ref_batch, bool tuned, amto_plan_s* donor,
+                        amto_plan_s** out);
+// A plan like `old` for new_batch (<= old's ref_batch) instances that takes
+// over old's constants and the state of old's instances keep[0..nkeep)
+// (ascending) as its instances 0..nkeep; the others start finished.  Runs on
+// stream s and waits for it.  On success old keeps only its per-instance
+// state (destroy it next); on failure old is unchanged.
+amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nkeep,
+                        cudaStream_t s, amto_plan_s** out);
 // iterate.cu
 amto_status configure_kernels(amto_plan_s* pl);
 void gemm_workspace(const amto_plan_s* pl, size_t* ws_floats, int* tiles);

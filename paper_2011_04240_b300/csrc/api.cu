@@ -2,9 +2,11 @@
 // sequence and its CUDA graph with a device-side loop condition.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "amto_internal.cuh"
 
@@ -296,46 +298,45 @@ amto_status solve_impl(amto_plan plan, int batch, const float* start, const floa
     return st;
 }
 
-}  // namespace amto
+// The plan's constant device arrays (basis matrices and the cached inverses
+// of Remarks 1-2): what a resized plan takes over from the plan it replaces.
+template <class F>
+void each_const(amto_plan_s* pl, F&& f) {
+    f(reinterpret_cast<void*&>(pl->P32));
+    f(reinterpret_cast<void*&>(pl->P64));
+    f(reinterpret_cast<void*&>(pl->Q32));
+    f(reinterpret_cast<void*&>(pl->A32));
+    f(reinterpret_cast<void*&>(pl->E0));
+    f(reinterpret_cast<void*&>(pl->Kag));
+    f(reinterpret_cast<void*&>(pl->Kinv64));
+    f(reinterpret_cast<void*&>(pl->Ktop));
+    f(reinterpret_cast<void*&>(pl->Kt_hi));
+    f(reinterpret_cast<void*&>(pl->Kt_lo));
+    f(reinterpret_cast<void*&>(pl->Kb_hi));
+    f(reinterpret_cast<void*&>(pl->Kb_lo));
+    f(reinterpret_cast<void*&>(pl->P32lo));
+}
 
-using namespace amto;
-
-extern "C" {
-
-const char* amto_last_error(void) { return g_last_error.c_str(); }
-
-const char* amto_version(void) { return "amto 0.1 (sm_103a)"; }
-
-amto_status amto_create(const amto_params* prm, amto_plan* out) {
-    clear_error();
-    if (!out) return einval("out is NULL");
+// A plan for the (validated) parameters p whose shape choices -- the pair
+// kernel's lane group, the apply kernel and its split over K, the block loop
+// -- are those of a batch of ref_batch instances (ref_batch >= p.max_batch),
+// so that an instance's arithmetic depends on ref_batch and not on the
+// allocated capacity.  With a donor (a plan of the same parameters and
+// ref_batch), the constants are taken over from it instead of recomputed:
+// the donor keeps its per-instance state and no constants afterwards.  On
+// failure the donor is unchanged.
+amto_status create_plan(const amto_params& p, int ref_batch, bool tuned, amto_plan_s* donor,
+                        amto_plan_s** out) {
     *out = nullptr;
-    if (!prm) return einval("params is NULL");
-    amto_params pp = *prm;
-    if (pp.planar == 1) pp.b = pp.a;  // disks: the kernels' l_z is l_xy (z unused)
-    if (amto::validate_params(pp) != AMTO_OK) return AMTO_EINVAL;
-    // automatic tile, apply and loop: the autotuner's cached choice for this
-    // shape, where one exists and is valid for these parameters
-    bool tuned = false;
-    {
-        amto_params t;
-        if (amto::tune_lookup(pp, &t)) {
-            if (amto::validate_params(t) == AMTO_OK) {
-                pp = t;
-                tuned = true;
-            } else {
-                clear_error();
-            }
-        }
-    }
-    const amto_params& p = pp;
-
+    amto_params pc = p;  // the parameters the shape choices see
+    pc.max_batch = ref_batch;
     amto_plan_s* pl = new (std::nothrow) amto_plan_s();
     if (!pl) {
         set_error("host allocation failed");
         return AMTO_ENOMEM;
     }
     pl->prm = p;
+    pl->ref_batch = ref_batch;
     pl->tuned = tuned;
     if (cudaGetDevice(&pl->device) != cudaSuccess) {
         cudaGetLastError();
@@ -351,8 +352,8 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     pl->nb = nb;
     pl->kdim = pl->n * (pl->nv + pl->nb);
     pl->p = pl->n * (pl->n - 1) / 2;
-    pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, p.max_batch,
-                              mult_aggregate(p), p.n_obstacles);
+    pl->geo = choose_geometry(pl->n, pl->m, p.tile_group, p.tile_time_blocks, ref_batch,
+                              mult_aggregate(pc), p.n_obstacles);
     pl->fused = apply_fused(p);
     {
         RhoSched& sc = pl->sched;
@@ -367,8 +368,8 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
         }
     }
     pl->kron = p.apply_mode == AMTO_APPLY_KRONECKER;
-    pl->block = loop_block(p);
-    pl->agg = mult_aggregate(p);
+    pl->block = loop_block(pc);
+    pl->agg = mult_aggregate(pc);
     pl->kp = (pl->kdim + 3) / 4 * 4;   // 16-byte rows for the tensor-memory-access descriptors
     pl->kp8 = (pl->kdim + 7) / 8 * 8;  // the same for 2-byte elements
     const bool tc = prec_tc(p.precision), bf = prec_bf16(p.precision);
@@ -383,27 +384,41 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
 #define ALLOC(ptr, count) \
     if (st == AMTO_OK) st = dalloc(pl, &(ptr), (count))
-    ALLOC(pl->P32, (size_t)pl->m * nv);
-    ALLOC(pl->P64, (size_t)pl->m * nv);
-    ALLOC(pl->Q32, (size_t)nv * nv);
-    ALLOC(pl->A32, (size_t)nb * nv);
-    ALLOC(pl->E0, (size_t)nv * nb);
     const int J = pl->sched.J;
     pl->ks_ag = (size_t)2 * nv * (nv + nb);
     pl->ks_top = nvn * kdim;
     pl->ks_tc = nvn * pl->kp;
     pl->ks_bf = nvn * pl->kp8;
-    ALLOC(pl->Kag, J * pl->ks_ag);
-    ALLOC(pl->Kinv64, (size_t)kdim * kdim);
-    ALLOC(pl->Ktop, J * pl->ks_top);
-    if (tc && !bf) {
-        ALLOC(pl->Kt_hi, J * pl->ks_tc);
-        ALLOC(pl->Kt_lo, J * pl->ks_tc);
-        ALLOC(pl->rhs_lo, (size_t)B * 3 * pl->kp);
+    if (donor) {  // shared until the new plan is complete, then owned by it
+        amto_plan_s* d = donor;
+        pl->P32 = d->P32; pl->P64 = d->P64; pl->Q32 = d->Q32; pl->A32 = d->A32; pl->E0 = d->E0;
+        pl->Kag = d->Kag; pl->Kinv64 = d->Kinv64; pl->Ktop = d->Ktop;
+        pl->Kt_hi = d->Kt_hi; pl->Kt_lo = d->Kt_lo; pl->Kb_hi = d->Kb_hi; pl->Kb_lo = d->Kb_lo;
+        pl->P32lo = d->P32lo;
+        pl->kkt_check = d->kkt_check;
+    } else {
+        ALLOC(pl->P32, (size_t)pl->m * nv);
+        ALLOC(pl->P64, (size_t)pl->m * nv);
+        ALLOC(pl->Q32, (size_t)nv * nv);
+        ALLOC(pl->A32, (size_t)nb * nv);
+        ALLOC(pl->E0, (size_t)nv * nb);
+        ALLOC(pl->Kag, J * pl->ks_ag);
+        ALLOC(pl->Kinv64, (size_t)kdim * kdim);
+        ALLOC(pl->Ktop, J * pl->ks_top);
+        if (tc && !bf) {
+            ALLOC(pl->Kt_hi, J * pl->ks_tc);
+            ALLOC(pl->Kt_lo, J * pl->ks_tc);
+        }
+        if (bf) {
+            ALLOC(pl->Kb_hi, J * pl->ks_bf);
+            ALLOC(pl->Kb_lo, J * pl->ks_bf);
+        }
+        ALLOC(pl->P32lo, (size_t)pl->m * nv);
+        pl->bytes_const = pl->bytes;
     }
+    // per-instance state
+    if (tc && !bf) ALLOC(pl->rhs_lo, (size_t)B * 3 * pl->kp);
     if (bf) {
-        ALLOC(pl->Kb_hi, J * pl->ks_bf);
-        ALLOC(pl->Kb_lo, J * pl->ks_bf);
         ALLOC(pl->rb_hi, (size_t)B * 3 * pl->kp8);
         ALLOC(pl->rb_lo, (size_t)B * 3 * pl->kp8);
     }
@@ -419,7 +434,6 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     ALLOC(pl->gpart, (size_t)B * pl->geo.n_chunks * 3 * nvn);
     ALLOC(pl->rpart, (size_t)B * pl->geo.n_chunks);
     ALLOC(pl->spart, (size_t)B * pl->geo.n_chunks);
-    ALLOC(pl->P32lo, (size_t)pl->m * nv);
     {
         const size_t ns = (size_t)final_free_ns(pl->geo, pl->n, pl->m);
         ALLOC(pl->fin, (size_t)B * ns * kFinRecFloats);
@@ -455,7 +469,7 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
         set_error("cudaMallocHost failed");
         st = AMTO_ENOMEM;
     }
-    if (st == AMTO_OK) st = precompute(pl);
+    if (st == AMTO_OK && !donor) st = precompute(pl);
     if (st == AMTO_OK && tc) st = tc_configure(pl);
     if (st == AMTO_OK && pl->block) st = configure_block_solver(pl);
     if (st == AMTO_OK && cudaMemset(pl->flags, 0, sizeof(int) * B) != cudaSuccess) {
@@ -468,12 +482,160 @@ amto_status amto_create(const amto_params* prm, amto_plan* out) {
     }
     if (st != AMTO_OK) {
         std::string keep = g_last_error;
+        if (donor) each_const(pl, [](void*& ptr) { ptr = nullptr; });  // still the donor's
         free_plan(pl);
         set_error(keep);
         return st;
     }
+    if (donor) {  // the constants change owner
+        each_const(donor, [](void*& ptr) { ptr = nullptr; });
+        pl->bytes_const = donor->bytes_const;
+        pl->bytes += donor->bytes_const;
+        donor->bytes -= donor->bytes_const;
+        donor->bytes_const = 0;
+    }
     *out = pl;
     return AMTO_OK;
+}
+
+// dst row i = src row keep[i], for i < nkeep (rows of `words` 32-bit words).
+__global__ void k_gather_rows(const unsigned* __restrict__ src, unsigned* __restrict__ dst,
+                              long long words, const int* __restrict__ keep, int nkeep) {
+    const long long total = words * nkeep;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / words, w = e - i * words;
+        dst[e] = src[(long long)keep[i] * words + w];
+    }
+}
+
+amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nkeep,
+                        cudaStream_t s, amto_plan_s** out) {
+    *out = nullptr;
+    if (new_batch < 1 || new_batch > 65535 || nkeep < 0 || nkeep > new_batch)
+        return einval("resize: 0 <= kept instances <= new capacity <= 65535");
+    if (new_batch > old->ref_batch)
+        return einval("resize: the new capacity exceeds the plan's reference batch");
+    for (int i = 0; i < nkeep; ++i)
+        if (keep[i] < 0 || keep[i] >= old->prm.max_batch || (i > 0 && keep[i] <= keep[i - 1]))
+            return einval("resize: kept instances must be ascending indexes of the old plan");
+    amto_params p = old->prm;
+    p.max_batch = new_batch;
+    amto_plan_s* pl = nullptr;
+    amto_status st = create_plan(p, old->ref_batch, old->tuned, old, &pl);
+    if (st != AMTO_OK) return st;  // the old plan is unchanged
+    // from here the new plan owns the constants; on failure they go back
+    auto fail = [&](const char* what) {
+        cudaGetLastError();
+        std::swap(old->bytes_const, pl->bytes_const);
+        old->bytes += old->bytes_const;
+        pl->bytes -= old->bytes_const;
+        std::vector<void**> a, b;
+        each_const(old, [&](void*& ptr) { a.push_back(&ptr); });
+        each_const(pl, [&](void*& ptr) { b.push_back(&ptr); });
+        for (size_t k = 0; k < a.size(); ++k) {
+            *a[k] = *b[k];
+            *b[k] = nullptr;
+        }
+        free_plan(pl);
+        set_error(std::string("resize: ") + what);
+        return AMTO_ECUDA;
+    };
+    const int B = new_batch, nvn = pl->n * pl->nv;
+    std::vector<int> fl((size_t)B, FLAG_DONE);  // every slot not kept starts finished
+    Ctl c{};
+    int* d_keep = nullptr;
+    if (cudaMalloc((void**)&d_keep, sizeof(int) * (size_t)(nkeep > 0 ? nkeep : 1)) != cudaSuccess)
+        return fail("cudaMalloc failed");
+    bool ok = cudaMemcpyAsync(d_keep, keep, sizeof(int) * (size_t)nkeep, cudaMemcpyHostToDevice,
+                              s) == cudaSuccess &&
+              cudaMemcpyAsync(pl->flags, fl.data(), sizeof(int) * (size_t)B,
+                              cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(&c, old->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    // the per-instance arrays that live from setup to the final residual
+    // (the final residual's screen records and work list and the split-K
+    // workspace are rebuilt by every launch that reads them); r64 is the FP64
+    // residual's running maximum, zeroed by the setup
+    struct Row {
+        void* src;
+        void* dst;
+        long long words;
+    };
+    const long long nobs5 = (long long)pl->prm.n_obstacles * 5;
+    const Row rows[] = {
+        {old->xi, pl->xi, 3LL * nvn},
+        {old->beq, pl->beq, 3LL * pl->n * pl->nb},
+        {old->obst, pl->obst, nobs5},
+        {old->lam[0], pl->lam[0], pl->agg ? 0 : (long long)pl->geo.lam_floats},
+        {old->lam[1], pl->lam[1], pl->agg ? 0 : (long long)pl->geo.lam_floats},
+        {old->Lagg, pl->Lagg, pl->agg ? 3LL * nvn : 0},
+        {old->gpart, pl->gpart, (long long)pl->geo.n_chunks * 3 * nvn},
+        {old->rpart, pl->rpart, (long long)pl->geo.n_chunks},
+        {old->spart, pl->spart, (long long)pl->geo.n_chunks},
+        {old->rhs, pl->rhs, 3LL * pl->kp},
+        {old->rhs_lo, pl->rhs_lo, pl->rhs_lo ? 3LL * pl->kp : 0},
+        {old->rb_hi, pl->rb_hi, pl->rb_hi ? 3LL * pl->kp8 / 2 : 0},
+        {old->rb_lo, pl->rb_lo, pl->rb_lo ? 3LL * pl->kp8 / 2 : 0},
+        {old->rmax, pl->rmax, 1}, {old->iters, pl->iters, 1}, {old->flags, pl->flags, 1},
+        {old->px3, pl->px3, 1}, {old->pbest, pl->pbest, 1}, {old->pat, pl->pat, 1},
+        {old->uticket, pl->uticket, 1}, {old->fin_olim, pl->fin_olim, 1},
+        {old->r64, pl->r64, 2},
+    };
+    for (const Row& r : rows) {
+        if (!ok) break;
+        if (r.words == 0 || nkeep == 0 || !r.src || !r.dst) continue;
+        const long long total = r.words * nkeep;
+        const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * pl->num_sms);
+        k_gather_rows<<<grid, 256, 0, s>>>((const unsigned*)r.src, (unsigned*)r.dst, r.words,
+                                           d_keep, nkeep);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    c.batch = B;
+    ok = ok && cudaMemcpy(pl->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice) == cudaSuccess;
+    cudaFree(d_keep);
+    if (!ok) return fail("moving the instances' state failed");
+    pl->trace = old->trace;
+    pl->obst_batch = 0;
+    if (pl->prm.n_obstacles > 0 && nkeep > 0 && keep[nkeep - 1] < old->obst_batch)
+        pl->obst_batch = nkeep;
+    *out = pl;
+    return AMTO_OK;
+}
+
+}  // namespace amto
+
+using namespace amto;
+
+extern "C" {
+
+const char* amto_last_error(void) { return g_last_error.c_str(); }
+
+const char* amto_version(void) { return "amto 0.1 (sm_103a)"; }
+
+amto_status amto_create(const amto_params* prm, amto_plan* out) {
+    clear_error();
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (!prm) return einval("params is NULL");
+    amto_params pp = *prm;
+    if (pp.planar == 1) pp.b = pp.a;  // disks: the kernels' l_z is l_xy (z unused)
+    if (amto::validate_params(pp) != AMTO_OK) return AMTO_EINVAL;
+    // automatic tile, apply and loop: the autotuner's cached choice for this
+    // shape, where one exists and is valid for these parameters
+    bool tuned = false;
+    {
+        amto_params t;
+        if (amto::tune_lookup(pp, &t)) {
+            if (amto::validate_params(t) == AMTO_OK) {
+                pp = t;
+                tuned = true;
+            } else {
+                clear_error();
+            }
+        }
+    }
+    return amto::create_plan(pp, pp.max_batch, tuned, nullptr, out);
 }
 
 void amto_destroy(amto_plan plan) {

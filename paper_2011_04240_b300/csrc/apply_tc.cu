@@ -385,9 +385,9 @@ void tc_shape(const amto_plan_s* pl, int batch, int* tm, int* tn, int* splits, i
     const int kbk = prec_bf16(pl->prm.precision) ? kRowBytes / 2 : kRowBytes / 4;
     *tm = (M + kBM - 1) / kBM;
     *tn = (N + kBN - 1) / kBN;
-    // the split over K is fixed by the plan's largest batch, so a column's
+    // the split over K is fixed by the plan's reference batch, so a column's
     // summation order (hence its result) does not depend on the batch size
-    const int tn_max = (3 * pl->prm.max_batch + kBN - 1) / kBN;
+    const int tn_max = (3 * pl->ref_batch + kBN - 1) / kBN;
     int sp = pl->num_sms / (*tm * tn_max);  // one wave of one-block-per-SM tiles
     sp = sp < 1 ? 1 : (sp > 8 ? 8 : sp);
     int kp = (K + sp - 1) / sp;

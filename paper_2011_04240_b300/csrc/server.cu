@@ -92,6 +92,13 @@ struct Result {
 
 struct Group {
     int n = 0, S = 0, nv = 0;
+    // memory admission: bytes of one resident instance; the capacity the
+    // count gets from an equal split of the budget (its fair share) and the
+    // largest it may reach (which fixes the plan's shape choices)
+    size_t per = 0;
+    int fair = 0, cap = 0;
+    amto_params prm{};       // the plan's parameters (max_batch aside), fixed at creation
+    bool tuned = false;
     amto_plan plan = nullptr;
     cudaStream_t stream = nullptr;
     float *d_start = nullptr, *d_goal = nullptr, *d_xi = nullptr, *d_resid = nullptr;
@@ -127,8 +134,9 @@ struct amto_server_s {
     bool stop = false;
     std::thread worker;
     int device = 0;
+    size_t budget = 0, used = 0;   // bytes of resident state: the budget and the slots' share
     // statistics (guarded by mu)
-    long long done_count = 0, done_iters = 0, chunks = 0;
+    long long done_count = 0, done_iters = 0, chunks = 0, resizes = 0;
     int worker_error = AMTO_OK;
     std::string worker_msg;
 };
@@ -157,56 +165,65 @@ amto_params plan_params(const amto_server_params& p, int n, int slots) {
     return ap;
 }
 
-amto_status group_init(amto_server_s* sv, Group& g, int n, int slots) {
-    const amto_server_params& p = sv->prm;
-    g.n = n;
-    g.S = slots;
-    g.nv = p.poly_degree + 1;
-    const amto_params ap = plan_params(p, n, slots);
-    amto_status st = amto_create(&ap, &g.plan);
-    if (st != AMTO_OK) return st;
-    amto_plan_s* pl = g.plan;
-    const size_t in = (size_t)slots * n * 3, out = (size_t)slots * 3 * n * g.nv;
-    AMTO_CUDA_TRY(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
-    AMTO_CUDA_TRY(cudaEventCreateWithFlags(&g.done_ev, cudaEventDisableTiming));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_start, 4 * in));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_goal, 4 * in));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_xi, 4 * out));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_resid, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_iters, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMalloc((void**)&g.d_list, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_start, 4 * in));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_goal, 4 * in));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_xi, 4 * out));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_resid, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_iters, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_flags, 4 * (size_t)slots));
-    AMTO_CUDA_TRY(cudaMallocHost((void**)&g.h_list, 4 * (size_t)slots));
-    g.slot_ticket.assign(slots, -1);
-    g.slot_admit.assign(slots, 0.0);
-    // every slot starts free (flagged done, skipped by all kernels); the
-    // group's stopping rule lives in the plan's control block
-    std::vector<int> fl(slots, FLAG_DONE);
-    AMTO_CUDA_TRY(cudaMemcpy(pl->flags, fl.data(), 4 * (size_t)slots, cudaMemcpyHostToDevice));
-    Ctl c{};
-    c.max_iters = p.max_iters;
-    c.tol = p.tol;
-    c.batch = slots;
-    AMTO_CUDA_TRY(cudaMemcpy(pl->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
-    // chunk graphs: C iterations of the batched step over slot prefixes 8,
-    // 16, 32, ... and S (the apply's split over K is fixed by S, so a slot's
-    // arithmetic is the same in every prefix)
-    for (int q = 8; q < slots; q *= 2) g.pre.push_back(q);
-    g.pre.push_back(slots);
-    for (int q : g.pre) {
+// Per-slot buffers of a group at capacity S (host staging, outputs, the
+// slot list) and its chunk graphs over slot prefixes [0, pre[k]) (pre
+// ascending, last = S): admission fills the lowest free slots, so at low load
+// a chunk launches over a short prefix instead of all S slots.  The apply's
+// split over K is fixed by the plan's reference batch, so a slot's arithmetic
+// is the same in every prefix and at every capacity.
+struct SlotBuffers {
+    float *d_start = nullptr, *d_goal = nullptr, *d_xi = nullptr, *d_resid = nullptr;
+    int *d_iters = nullptr, *d_list = nullptr;
+    float *h_start = nullptr, *h_goal = nullptr, *h_xi = nullptr, *h_resid = nullptr;
+    int *h_iters = nullptr, *h_flags = nullptr, *h_list = nullptr;
+    std::vector<int> pre;
+    std::vector<cudaGraphExec_t> chunk;
+};
+
+void buffers_free(SlotBuffers& b) {
+    for (cudaGraphExec_t ex : b.chunk) cudaGraphExecDestroy(ex);
+    b.chunk.clear();
+    void* d[] = {b.d_start, b.d_goal, b.d_xi, b.d_resid, b.d_iters, b.d_list};
+    for (void* p : d)
+        if (p) cudaFree(p);
+    void* h[] = {b.h_start, b.h_goal, b.h_xi, b.h_resid, b.h_iters, b.h_flags, b.h_list};
+    for (void* p : h)
+        if (p) cudaFreeHost(p);
+    b = SlotBuffers();
+}
+
+amto_status buffers_alloc(SlotBuffers& b, int n, int nv, int S) {
+    const size_t in = (size_t)S * n * 3, out = (size_t)S * 3 * n * nv;
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_start, 4 * in));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_goal, 4 * in));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_xi, 4 * out));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_resid, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_iters, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMalloc((void**)&b.d_list, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_start, 4 * in));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_goal, 4 * in));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_xi, 4 * out));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_resid, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_iters, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_flags, 4 * (size_t)S));
+    AMTO_CUDA_TRY(cudaMallocHost((void**)&b.h_list, 4 * (size_t)S));
+    return AMTO_OK;
+}
+
+amto_status buffers_graphs(SlotBuffers& b, amto_plan_s* pl, int S, int chunk_iters,
+                           cudaStream_t stream) {
+    for (int q = 8; q < S; q *= 2) b.pre.push_back(q);
+    b.pre.push_back(S);
+    for (int q : b.pre) {
+        amto_status st = AMTO_OK;
         cudaGraph_t graph;
-        AMTO_CUDA_TRY(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
-        for (int it = 0; it < p.chunk_iters && st == AMTO_OK; ++it) {
-            st = launch_rhs(pl, q, g.stream);
-            if (st == AMTO_OK) st = launch_apply(pl, q, g.stream);
-            if (st == AMTO_OK) st = launch_pair(pl, q, 0, nullptr, 0, 0, g.stream);
+        AMTO_CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < chunk_iters && st == AMTO_OK; ++it) {
+            st = launch_rhs(pl, q, stream);
+            if (st == AMTO_OK) st = launch_apply(pl, q, stream);
+            if (st == AMTO_OK) st = launch_pair(pl, q, 0, nullptr, 0, 0, stream);
         }
-        cudaError_t ce = cudaStreamEndCapture(g.stream, &graph);
+        cudaError_t ce = cudaStreamEndCapture(stream, &graph);
         if (st != AMTO_OK) return st;
         if (ce != cudaSuccess) {
             set_error("server: capture of the iteration chunk failed");
@@ -219,29 +236,199 @@ amto_status group_init(amto_server_s* sv, Group& g, int n, int slots) {
             set_error("server: instantiating the iteration chunk failed");
             return AMTO_ECUDA;
         }
-        g.chunk.push_back(ex);
+        b.chunk.push_back(ex);
     }
     return AMTO_OK;
 }
 
+void buffers_take(Group& g, SlotBuffers& b) {
+    g.d_start = b.d_start; g.d_goal = b.d_goal; g.d_xi = b.d_xi; g.d_resid = b.d_resid;
+    g.d_iters = b.d_iters; g.d_list = b.d_list;
+    g.h_start = b.h_start; g.h_goal = b.h_goal; g.h_xi = b.h_xi; g.h_resid = b.h_resid;
+    g.h_iters = b.h_iters; g.h_flags = b.h_flags; g.h_list = b.h_list;
+    g.pre = std::move(b.pre);
+    g.chunk = std::move(b.chunk);
+    b = SlotBuffers();
+}
+
+SlotBuffers buffers_of(Group& g) {
+    SlotBuffers b;
+    b.d_start = g.d_start; b.d_goal = g.d_goal; b.d_xi = g.d_xi; b.d_resid = g.d_resid;
+    b.d_iters = g.d_iters; b.d_list = g.d_list;
+    b.h_start = g.h_start; b.h_goal = g.h_goal; b.h_xi = g.h_xi; b.h_resid = g.h_resid;
+    b.h_iters = g.h_iters; b.h_flags = g.h_flags; b.h_list = g.h_list;
+    b.pre = std::move(g.pre);
+    b.chunk = std::move(g.chunk);
+    g.d_start = g.d_goal = g.d_xi = g.d_resid = nullptr;
+    g.d_iters = g.d_list = nullptr;
+    g.h_start = g.h_goal = g.h_xi = g.h_resid = nullptr;
+    g.h_iters = g.h_flags = g.h_list = nullptr;
+    g.pre.clear();
+    g.chunk.clear();
+    return b;
+}
+
+amto_status group_init(amto_server_s* sv, Group& g, int slots) {
+    const amto_server_params& p = sv->prm;
+    g.S = slots;
+    g.nv = p.poly_degree + 1;
+    amto_params ap = g.prm;
+    ap.max_batch = slots;
+    amto_status st = create_plan(ap, g.cap, g.tuned, nullptr, &g.plan);
+    if (st != AMTO_OK) return st;
+    amto_plan_s* pl = g.plan;
+    AMTO_CUDA_TRY(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    AMTO_CUDA_TRY(cudaEventCreateWithFlags(&g.done_ev, cudaEventDisableTiming));
+    SlotBuffers b;
+    st = buffers_alloc(b, g.n, g.nv, slots);
+    if (st == AMTO_OK) st = buffers_graphs(b, pl, slots, p.chunk_iters, g.stream);
+    if (st != AMTO_OK) {
+        buffers_free(b);
+        return st;
+    }
+    buffers_take(g, b);
+    g.slot_ticket.assign(slots, -1);
+    g.slot_admit.assign(slots, 0.0);
+    // every slot starts free (flagged done, skipped by all kernels); the
+    // group's stopping rule lives in the plan's control block
+    std::vector<int> fl(slots, FLAG_DONE);
+    AMTO_CUDA_TRY(cudaMemcpy(pl->flags, fl.data(), 4 * (size_t)slots, cudaMemcpyHostToDevice));
+    Ctl c{};
+    c.max_iters = p.max_iters;
+    c.tol = p.tol;
+    c.batch = slots;
+    AMTO_CUDA_TRY(cudaMemcpy(pl->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    return AMTO_OK;
+}
+
 void group_free(Group& g) {
-    for (cudaGraphExec_t ex : g.chunk) cudaGraphExecDestroy(ex);
+    SlotBuffers b = buffers_of(g);
+    buffers_free(b);
     if (g.done_ev) cudaEventDestroy(g.done_ev);
-    void* d[] = {g.d_start, g.d_goal, g.d_xi, g.d_resid, g.d_iters, g.d_list};
-    for (void* p : d)
-        if (p) cudaFree(p);
-    void* h[] = {g.h_start, g.h_goal, g.h_xi, g.h_resid, g.h_iters, g.h_flags, g.h_list};
-    for (void* p : h)
-        if (p) cudaFreeHost(p);
     if (g.stream) cudaStreamDestroy(g.stream);
     if (g.plan) amto_destroy(g.plan);
 }
 
+// Change a group's capacity to S between chunks (its stream idle): a new
+// plan at capacity S takes over the cached inverse and the resident
+// instances' state (compacted to the lowest slots), new chunk graphs are
+// captured, and the old plan is freed.  Returns AMTO_OK with the group
+// unchanged if the device has no room for the new state.
+amto_status group_resize(amto_server_s* sv, Group& g, int S) {
+    AMTO_CUDA_TRY(cudaStreamSynchronize(g.stream));
+    std::vector<int> keep;
+    for (int s = 0; s < g.S; ++s)
+        if (g.slot_ticket[s] >= 0) keep.push_back(s);
+    if ((int)keep.size() > S || S == g.S) return AMTO_OK;
+    SlotBuffers b;
+    amto_status st = buffers_alloc(b, g.n, g.nv, S);
+    amto_plan_s* np = nullptr;
+    if (st == AMTO_OK) st = plan_resize(g.plan, S, keep.data(), (int)keep.size(), g.stream, &np);
+    if (st != AMTO_OK) {
+        buffers_free(b);
+        if (st == AMTO_ECUDA) return st;
+        clear_error();  // no room: keep the current capacity
+        return AMTO_OK;
+    }
+    st = buffers_graphs(b, np, S, sv->prm.chunk_iters, g.stream);
+    if (st != AMTO_OK) {
+        buffers_free(b);
+        amto_destroy(np);
+        return st;
+    }
+    amto_destroy(g.plan);  // its per-instance state; the constants now belong to np
+    g.plan = np;
+    SlotBuffers ob = buffers_of(g);
+    buffers_free(ob);
+    buffers_take(g, b);
+    std::vector<int64_t> tk(S, -1);
+    std::vector<double> ad(S, 0.0);
+    for (size_t i = 0; i < keep.size(); ++i) {
+        tk[i] = g.slot_ticket[keep[i]];
+        ad[i] = g.slot_admit[keep[i]];
+    }
+    g.slot_ticket = std::move(tk);
+    g.slot_admit = std::move(ad);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->used = sv->used - (size_t)g.S * g.per + (size_t)S * g.per;
+    g.S = S;
+    sv->resizes += 1;
+    return AMTO_OK;
+}
+
+int pow2_at_least(int v) {
+    int q = 1;
+    while (q < v) q *= 2;
+    return q;
+}
+
+// Shared memory budget (between chunks, every stream idle).  The count with
+// the most queued requests beyond its free slots doubles its capacity (at
+// least to the next power of two above its resident and queued requests; at
+// most its largest capacity), from unclaimed budget and from the other
+// counts: an idle count (empty queue) gives up free slots down to
+// max(min(8, its fair share), the next power of two >= its resident
+// instances); a count with a queue keeps at least its fair share.  A donor
+// gives up slots only where that frees a quarter of its capacity or more, and
+// a count grows only by a quarter of its capacity or more.  At most one count
+// grows per chunk.
+amto_status rebalance(amto_server_s* sv) {
+    Group* grow = nullptr;
+    size_t unmet_best = 0;
+    for (auto& gp : sv->groups) {
+        Group& g = *gp;
+        const size_t freeslots = (size_t)(g.S - g.active);
+        if (g.S < g.cap && g.queue.size() > freeslots &&
+            g.queue.size() - freeslots > unmet_best) {
+            unmet_best = g.queue.size() - freeslots;
+            grow = &g;
+        }
+    }
+    if (!grow) return AMTO_OK;
+    Group& g = *grow;
+    const int target =
+        std::min(g.cap, std::max(2 * g.S, pow2_at_least(g.active + (int)g.queue.size())));
+    // donors, most reclaimable bytes first
+    std::vector<std::pair<size_t, Group*>> donors;
+    size_t room = sv->budget > sv->used ? sv->budget - sv->used : 0, avail = room;
+    for (auto& hp : sv->groups) {
+        Group& h = *hp;
+        if (&h == &g) continue;
+        int floor_h = h.queue.empty()
+                          ? std::max(std::min(8, h.fair), pow2_at_least(std::max(h.active, 1)))
+                          : std::max(h.fair, h.active);
+        floor_h = std::min(floor_h, h.S);
+        if (h.S - floor_h >= std::max(1, h.S / 4)) {
+            donors.push_back({(size_t)(h.S - floor_h) * h.per, &h});
+            avail += (size_t)(h.S - floor_h) * h.per;
+        }
+    }
+    // grow by a quarter of the capacity at least, or not at all
+    const int reach = (int)std::min<size_t>((size_t)target, (size_t)g.S + avail / g.per);
+    if (reach < g.S + std::max(1, g.S / 4)) return AMTO_OK;
+    const size_t need = (size_t)(reach - g.S) * g.per;
+    std::sort(donors.begin(), donors.end(),
+              [](const std::pair<size_t, Group*>& a, const std::pair<size_t, Group*>& b) {
+                  return a.first > b.first;
+              });
+    for (auto& d : donors) {
+        if (room >= need) break;
+        Group& h = *d.second;
+        amto_status st = group_resize(sv, h, h.S - (int)(d.first / h.per));
+        if (st != AMTO_OK) return st;
+        room = sv->budget > sv->used ? sv->budget - sv->used : 0;
+    }
+    const int S = (int)std::min<size_t>((size_t)reach, (size_t)g.S + room / g.per);
+    if (S > g.S) return group_resize(sv, g, S);
+    return AMTO_OK;
+}
+
 // Admit queued requests into free slots of one group (worker thread).
-amto_status admit(amto_server_s* sv, Group& g) {
+// At most `limit` instances resident after admission.
+amto_status admit(amto_server_s* sv, Group& g, int limit) {
     int cnt = 0;
     const int n = g.n;
-    for (int s = 0; s < g.S && !g.queue.empty(); ++s) {
+    for (int s = 0; s < g.S && !g.queue.empty() && g.active + cnt < limit; ++s) {
         if (g.slot_ticket[s] >= 0) continue;
         Pending p = std::move(g.queue.front());
         g.queue.pop_front();
@@ -340,10 +527,16 @@ void worker_main(amto_server_s* sv) {
                 }
             }
         }
+        // a count waiting below its fair share stops the counts above theirs
+        // from admitting beyond them, so their capacity drains back to it
+        bool starved = false;
+        for (auto& gp : sv->groups)
+            if (gp->S < gp->fair && gp->queue.size() > (size_t)(gp->S - gp->active)) starved = true;
         // admit, then one chunk per group with resident work (groups overlap)
         for (auto& gp : sv->groups) {
             Group& g = *gp;
-            if (st == AMTO_OK) st = admit(sv, g);
+            const int limit = starved && g.S > g.fair ? g.fair : g.S;
+            if (st == AMTO_OK) st = admit(sv, g, limit);
             if (st == AMTO_OK && g.active > 0) {
                 any = true;
                 int hi = 0;
@@ -376,6 +569,7 @@ void worker_main(amto_server_s* sv) {
             }
             st = retire(sv, g);
         }
+        if (st == AMTO_OK && sv->prm.admission == AMTO_ADMIT_SHARED) st = rebalance(sv);
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->chunks += 1;
     }
@@ -416,6 +610,10 @@ amto_status amto_server_create(const amto_server_params* prm, amto_server* out) 
         set_error("invalid argument: max_slots must be in [1, 65535]");
         return AMTO_EINVAL;
     }
+    if (p.admission != AMTO_ADMIT_SHARED && p.admission != AMTO_ADMIT_FIXED) {
+        set_error("invalid argument: admission must be AMTO_ADMIT_SHARED or AMTO_ADMIT_FIXED");
+        return AMTO_EINVAL;
+    }
     for (int i = 0; i < p.n_sizes; ++i) {
         for (int j = 0; j < i; ++j)
             if (p.sizes[i] == p.sizes[j]) {
@@ -433,14 +631,16 @@ amto_status amto_server_create(const amto_server_params* prm, amto_server* out) 
     sv->prm = p;
     sv->sizes.assign(p.sizes, p.sizes + p.n_sizes);
     cudaGetDevice(&sv->device);
-    // admission by device memory: each agent count gets an equal share of the
-    // budget; its slot count is the number of resident instances that fit
+    // admission by device memory: each agent count starts at an equal share
+    // of the budget (its fair share, the instances that fit in it); with the
+    // shared budget a count may grow to the whole budget (at most max_slots)
     size_t budget = p.memory_budget;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
         budget = fr / 2;
     }
+    sv->budget = budget;
     const size_t share = budget / p.n_sizes;
     amto_status st = AMTO_OK;
     sv->inbox.resize(p.n_sizes);
@@ -448,9 +648,11 @@ amto_status amto_server_create(const amto_server_params* prm, amto_server* out) 
         const int n = p.sizes[i];
         const size_t per = instance_bytes(n, p.m_steps, p.poly_degree, AMTO_BC_ALL, p.precision,
                                           p.proj_mode);
-        long long slots = (long long)(share / per);
-        if (slots > p.max_slots) slots = p.max_slots;
-        if (slots < 1) {
+        const long long fair = std::min<long long>((long long)(share / per), p.max_slots);
+        const long long cap = p.admission == AMTO_ADMIT_FIXED
+                                  ? fair
+                                  : std::min<long long>((long long)(budget / per), p.max_slots);
+        if (fair < 1) {
             set_error("server: the memory budget does not fit one instance of " + std::to_string(n) +
                       " agents");
             st = AMTO_ENOMEM;
@@ -458,7 +660,23 @@ amto_status amto_server_create(const amto_server_params* prm, amto_server* out) 
         }
         sv->groups.emplace_back(new Group());
         sv->group_of_n[n] = i;
-        st = group_init(sv, *sv->groups.back(), n, (int)slots);
+        Group& g = *sv->groups.back();
+        g.n = n;
+        g.per = per;
+        g.fair = (int)fair;
+        g.cap = (int)cap;
+        // the shape choices (and a tuned choice, where the autotuner's cache
+        // has one) are those of the largest capacity, fixed for the server's life
+        g.prm = plan_params(p, n, g.cap);
+        amto_params t;
+        if (tune_lookup(g.prm, &t) && validate_params(t) == AMTO_OK) {
+            g.prm = t;
+            g.tuned = true;
+        }
+        clear_error();
+        st = validate_params(g.prm);
+        if (st == AMTO_OK) st = group_init(sv, g, g.fair);
+        if (st == AMTO_OK) sv->used += (size_t)g.S * per;
     }
     if (st != AMTO_OK) {
         std::string keep = amto_last_error();
@@ -554,7 +772,12 @@ amto_status amto_server_stats(amto_server sv, amto_server_stats_t* out) {
     for (int i = 0; i < (int)sv->groups.size() && i < 32; ++i) {
         out->sizes[i] = sv->groups[i]->n;
         out->slots[i] = sv->groups[i]->S;
+        out->fair_slots[i] = sv->groups[i]->fair;
+        out->max_capacity[i] = sv->groups[i]->cap;
     }
+    out->resizes = sv->resizes;
+    out->budget = sv->budget;
+    out->budget_used = sv->used;
     return AMTO_OK;
 }
 

@@ -177,6 +177,7 @@ extern "C" amto_status amto_solve_static(amto_plan plan, const float* start, con
     amto_plan_s v;
     v.prm = pl.prm;
     v.prm.max_batch = 1;  // one instance: the apply runs as the matrix-vector kernel
+    v.ref_batch = 1;
     v.device = pl.device;
     v.num_sms = pl.num_sms;
     v.n = pl.n; v.m = pl.m; v.N = pl.N; v.nv = pl.nv; v.nb = pl.nb; v.kdim = pl.kdim; v.p = pl.p;

@@ -101,7 +101,8 @@ def _server_params(**kw):
 @pytest.mark.parametrize("bad", [dict(sizes=()), dict(sizes=(8, 8)), dict(sizes=(1,)),
                                  dict(sizes=(8, 300)), dict(chunk_iters=0), dict(max_iters=0),
                                  dict(tol=float("nan")), dict(max_slots=0), dict(m_steps=5),
-                                 dict(precision=9), dict(proj_mode=3), dict(n_sizes=40)])
+                                 dict(precision=9), dict(proj_mode=3), dict(n_sizes=40),
+                                 dict(admission=2)])
 def test_server_create_rejects_invalid_params(lib, bad):
     """Checked before any device call, so this runs without a GPU."""
     from paper_2011_04240_b300 import amto

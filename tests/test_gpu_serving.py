@@ -172,3 +172,73 @@ def test_rejects_unserved_size_and_unknown_ticket():
         assert st == A.EINVAL
     finally:
         sv.close()
+
+
+def _per_instance_bytes(n, precision="fp32", proj=0):
+    """Device bytes of one resident instance, as the server accounts them."""
+    sv = _server((n,), precision, proj_mode=proj, max_slots=4, memory_budget=1 << 30)
+    try:
+        st = sv.stats()
+        return st["budget_used"] // st["slots"][n]
+    finally:
+        sv.close()
+
+
+@pytest.mark.parametrize("precision,proj", [("fp32", 0), ("tf32x3", 1)])
+def test_shared_budget_moves_capacity_without_changing_results(precision, proj):
+    """Shared admission: a flooded count grows by taking the idle count's
+    free slots, then the other way round; every request's result is bitwise
+    the one of a server whose budget never forces a resize (the shape choices
+    of both are fixed by the same largest capacity, 32 slots)."""
+    kw = dict(proj_mode=proj, max_slots=32, chunk_iters=4, max_iters=60, tol=1e-2)
+    per16 = _per_instance_bytes(16, precision, proj)
+    tight = _server((8, 16), precision, memory_budget=40 * per16, **kw)
+    roomy = _server((8, 16), precision, memory_budget=1 << 30, **kw)
+    try:
+        s0 = tight.stats()
+        assert s0["fair_slots"][16] == 20 and s0["max_capacity"][16] == 32, s0
+        assert s0["slots"][16] == 20 and s0["max_capacity"][8] == 32, s0
+        assert roomy.stats()["slots"] == {8: 32, 16: 32}
+        res = {}
+        for phase, n in enumerate((16, 8)):
+            probs = [W.random_box(n, 3000 + 100 * phase + i, box=(8.0, 8.0, 4.0))
+                     for i in range(70)]
+            out = []
+            for sv in (tight, roomy):
+                out.append(_collect(sv, [sv.submit(p.start, p.goal) for p in probs]))
+            res[n] = out
+            st = tight.stats()
+            assert st["budget_used"] <= st["budget"], st
+            if n == 16:
+                assert st["slots"][16] == 32 and st["slots"][8] < 32, st
+            else:
+                assert st["slots"][8] > 8 and st["slots"][16] < 32, st
+        assert tight.stats()["resizes"] >= 3
+        assert roomy.stats()["resizes"] == 0
+        for n, (a, b) in res.items():
+            for (ta, ra), (tb, rb) in zip(a.items(), b.items()):
+                assert ra["status"] == rb["status"] == 0
+                assert ra["iters"] == rb["iters"]
+                assert ra["resid"] == rb["resid"]
+                assert np.array_equal(ra["xi"], rb["xi"]), (n, ta)
+    finally:
+        tight.close()
+        roomy.close()
+
+
+def test_fixed_admission_keeps_equal_shares():
+    """AMTO_ADMIT_FIXED: a flooded count keeps its equal share."""
+    from paper_2011_04240_b300.amto import ADMIT_FIXED
+    per16 = _per_instance_bytes(16)
+    sv = _server((8, 16), max_slots=32, max_iters=20, tol=0.0, memory_budget=40 * per16,
+                 admission=ADMIT_FIXED)
+    try:
+        s0 = sv.stats()
+        assert s0["slots"][16] == s0["max_capacity"][16] == 20, s0
+        probs = [W.random_box(16, 4100 + i, box=(8.0, 8.0, 4.0)) for i in range(50)]
+        res = _collect(sv, [sv.submit(p.start, p.goal) for p in probs])
+        assert all(r["iters"] == 20 for r in res.values())
+        st = sv.stats()
+        assert st["resizes"] == 0 and st["slots"] == s0["slots"], st
+    finally:
+        sv.close()
