@@ -242,3 +242,27 @@ def test_fixed_admission_keeps_equal_shares():
         assert st["resizes"] == 0 and st["slots"] == s0["slots"], st
     finally:
         sv.close()
+
+
+def test_resize_keeps_rho_schedule_results():
+    """Shared admission with the per-request rho schedule (structured apply,
+    each slot at its own stage): results across resizes are bitwise those of
+    a server that never resizes."""
+    kw = dict(max_slots=16, chunk_iters=3, max_iters=12, tol=0.0, rho_stages=4,
+              rho_growth=3.0, rho_stage_iters=3)
+    per12 = _per_instance_bytes(12)
+    tight = _server((5, 12), memory_budget=24 * per12, **kw)
+    roomy = _server((5, 12), memory_budget=1 << 30, **kw)
+    try:
+        assert tight.stats()["slots"][12] < 16 and roomy.stats()["slots"] == {5: 16, 12: 16}
+        probs = [W.random_box(12, 5200 + i, box=(8.0, 8.0, 4.0)) for i in range(40)]
+        out = [_collect(sv, [sv.submit(p.start, p.goal) for p in probs]) for sv in (tight, roomy)]
+        st = tight.stats()
+        assert st["resizes"] >= 1 and st["slots"][12] == 16, st
+        for ra, rb in zip(out[0].values(), out[1].values()):
+            assert ra["iters"] == rb["iters"] == 12
+            assert ra["resid"] == rb["resid"]
+            assert np.array_equal(ra["xi"], rb["xi"])
+    finally:
+        tight.close()
+        roomy.close()
