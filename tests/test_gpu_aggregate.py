@@ -66,7 +66,9 @@ def test_automatic_choice_and_rejections():
     (W.random_box(33, 23, box=(8.0, 8.0, 4.0), m=41, T=6.0), 30, "fp32"),
     (W.random_box(16, 21, box=(6.0, 6.0, 3.0)), 60, "fp32"),
     (W.random_box(24, 5, box=(8.0, 8.0, 4.0), m=57, T=6.0), 25, "tf32x3"),
-    (W.random_box(2, 8, box=(3.0, 3.0, 2.0), m=20, T=3.0), 15, "fp32")])
+    (W.random_box(2, 8, box=(3.0, 3.0, 2.0), m=20, T=3.0), 15, "fp32"),
+    # 100 agents: lane group 8, 13 agent blocks (the last padded), paired own blocks
+    (W.random_box(100, 31, box=(16.0, 16.0, 8.0)), 5, "fp32")])
 def test_matches_oracle(prob, k, precision):
     amto = _amto()
     pl = planner(prob, "R3", precision=precision, loop_mode=1)
@@ -80,7 +82,11 @@ def test_matches_oracle(prob, k, precision):
 
 @pytest.mark.parametrize("n,B,precision,apply_mode,k", [
     (64, 8, "fp32", 0, 20), (64, 6, "tf32x3", 0, 10), (32, 12, "fp32", 3, 40),
-    (24, 5, "bf16x3", 0, 10), (16, 40, "fp32", 0, 50)])
+    (24, 5, "bf16x3", 0, 10), (16, 40, "fp32", 0, 50),
+    # lane group 16, four agent blocks: paired own blocks on four of six tiles
+    (64, 64, "tf32x3", 0, 10),
+    # lane group 8, 13 blocks (odd, the last padded): paired tiles with masks
+    (100, 4, "fp32", 0, 10)])
 def test_tracks_the_per_pair_form(n, B, precision, apply_mode, k):
     """Same batch through both forms: the float32 iterates agree to rounding.
     (Random boxes: on the antipodal sphere shell float32 rounding of either
@@ -88,7 +94,7 @@ def test_tracks_the_per_pair_form(n, B, precision, apply_mode, k):
     alike after a few iterations; that case is compared at k <= 3 above.)"""
     from paper_2011_04240_b300 import Planner
     amto = _amto()
-    box = (12.0, 12.0, 6.0) if n == 64 else (8.0, 8.0, 4.0)
+    box = (12.0, 12.0, 6.0) if n == 64 else (16.0, 16.0, 8.0) if n > 64 else (8.0, 8.0, 4.0)
     probs = [W.random_box(n, 700 + i, box=box) for i in range(B)]
     p0 = probs[0]
     prec = {"fp32": 0, "tf32x3": 1, "bf16x3": 2}[precision]
@@ -96,6 +102,10 @@ def test_tracks_the_per_pair_form(n, B, precision, apply_mode, k):
                               max_batch=B, precision=prec, apply_mode=apply_mode, loop_mode=1,
                               multipliers=mult)
     pa, pp = mk(amto.MULT_AGGREGATE), mk(amto.MULT_PAIRS)
+    if n == 64 and B == 64:
+        assert pa.info.group == 16
+    if n == 100:
+        assert pa.info.group == 8
     xa, ra, ka = gpu_solve(pa, probs, k)
     xp, rp, kp = gpu_solve(pp, probs, k)
     assert np.all(ka == k) and np.all(kp == k)
