@@ -78,6 +78,7 @@ def parse():
 
 SERVE_SIZES = (8, 16, 32, 48, 64)
 SERVE_TOL, SERVE_MAX_ITERS = 1e-2, 2000
+SERVE_CHUNK = 32  # iterations between admission points (of 8-64: the lowest p99 at 200-5000 req/s)
 SERVE_POOL = 1000  # distinct problems per agent count; longer runs cycle through them
 _serve_pool = {}
 
@@ -112,7 +113,7 @@ def serving_compare(rate, seconds, precision, seed=0, seq_cap=400, rho_schedule=
 
     def serve(**kw):
         sv = Server(SERVE_SIZES, m_steps=100, T=8.0, proj_mode=amto.PROJ_LITERAL,
-                    precision=prec, max_slots=256, chunk_iters=8, max_iters=SERVE_MAX_ITERS,
+                    precision=prec, max_slots=256, chunk_iters=SERVE_CHUNK, max_iters=SERVE_MAX_ITERS,
                     tol=SERVE_TOL, **kw)
         try:
             for p in warm:
