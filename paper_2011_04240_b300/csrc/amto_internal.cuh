@@ -308,6 +308,9 @@ amto_status create_plan(const amto_params& p, int ref_batch, bool tuned, amto_pl
 // state (destroy it next); on failure old is unchanged.
 amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nkeep,
                         cudaStream_t s, amto_plan_s** out);
+// Undo a resize: the constants go back from pl to old (which kept its
+// state), and pl is freed.
+void plan_give_back(amto_plan_s* pl, amto_plan_s* old);
 // iterate.cu
 amto_status configure_kernels(amto_plan_s* pl);
 void gemm_workspace(const amto_plan_s* pl, size_t* ws_floats, int* tiles);

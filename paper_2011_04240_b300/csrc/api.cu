@@ -509,6 +509,22 @@ __global__ void k_gather_rows(const unsigned* __restrict__ src, unsigned* __rest
     }
 }
 
+void plan_give_back(amto_plan_s* pl, amto_plan_s* old) {
+    std::swap(old->bytes_const, pl->bytes_const);
+    old->bytes += old->bytes_const;
+    pl->bytes -= old->bytes_const;
+    std::vector<void**> a, b;
+    each_const(old, [&](void*& ptr) { a.push_back(&ptr); });
+    each_const(pl, [&](void*& ptr) { b.push_back(&ptr); });
+    for (size_t k = 0; k < a.size(); ++k) {
+        *a[k] = *b[k];
+        *b[k] = nullptr;
+    }
+    DeviceGuard g(pl->device);
+    cudaDeviceSynchronize();
+    free_plan(pl);
+}
+
 amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nkeep,
                         cudaStream_t s, amto_plan_s** out) {
     *out = nullptr;
@@ -525,28 +541,18 @@ amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nk
     amto_status st = create_plan(p, old->ref_batch, old->tuned, old, &pl);
     if (st != AMTO_OK) return st;  // the old plan is unchanged
     // from here the new plan owns the constants; on failure they go back
-    auto fail = [&](const char* what) {
+    auto fail = [&](const char* what, amto_status st) {
         cudaGetLastError();
-        std::swap(old->bytes_const, pl->bytes_const);
-        old->bytes += old->bytes_const;
-        pl->bytes -= old->bytes_const;
-        std::vector<void**> a, b;
-        each_const(old, [&](void*& ptr) { a.push_back(&ptr); });
-        each_const(pl, [&](void*& ptr) { b.push_back(&ptr); });
-        for (size_t k = 0; k < a.size(); ++k) {
-            *a[k] = *b[k];
-            *b[k] = nullptr;
-        }
-        free_plan(pl);
+        plan_give_back(pl, old);
         set_error(std::string("resize: ") + what);
-        return AMTO_ECUDA;
+        return st;
     };
     const int B = new_batch, nvn = pl->n * pl->nv;
     std::vector<int> fl((size_t)B, FLAG_DONE);  // every slot not kept starts finished
     Ctl c{};
     int* d_keep = nullptr;
     if (cudaMalloc((void**)&d_keep, sizeof(int) * (size_t)(nkeep > 0 ? nkeep : 1)) != cudaSuccess)
-        return fail("cudaMalloc failed");
+        return fail("cudaMalloc failed", AMTO_ENOMEM);
     bool ok = cudaMemcpyAsync(d_keep, keep, sizeof(int) * (size_t)nkeep, cudaMemcpyHostToDevice,
                               s) == cudaSuccess &&
               cudaMemcpyAsync(pl->flags, fl.data(), sizeof(int) * (size_t)B,
@@ -594,7 +600,7 @@ amto_status plan_resize(amto_plan_s* old, int new_batch, const int* keep, int nk
     c.batch = B;
     ok = ok && cudaMemcpy(pl->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice) == cudaSuccess;
     cudaFree(d_keep);
-    if (!ok) return fail("moving the instances' state failed");
+    if (!ok) return fail("moving the instances' state failed", AMTO_ECUDA);
     pl->trace = old->trace;
     pl->obst_batch = 0;
     if (pl->prm.n_obstacles > 0 && nkeep > 0 && keep[nkeep - 1] < old->obst_batch)

@@ -331,10 +331,11 @@ amto_status group_resize(amto_server_s* sv, Group& g, int S) {
         return AMTO_OK;
     }
     st = buffers_graphs(b, np, S, sv->prm.chunk_iters, g.stream);
-    if (st != AMTO_OK) {
+    if (st != AMTO_OK) {  // keep the current capacity: the constants go back
         buffers_free(b);
-        amto_destroy(np);
-        return st;
+        plan_give_back(np, g.plan);
+        clear_error();
+        return AMTO_OK;
     }
     amto_destroy(g.plan);  // its per-instance state; the constants now belong to np
     g.plan = np;
