@@ -153,12 +153,6 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long bars[2 * kTcStages + 1];
     __shared__ unsigned tmem_slot;
-    griddep_wait();
-    const int stage = A.ctl->stage;  // rho stage of this QP solve (the batch is in step)
-    const CUtensorMap& ta_hi = TM.a_hi[stage];
-    const CUtensorMap& ta_lo = TM.a_lo[stage];
-    const CUtensorMap& tb_hi = TM.b_hi;
-    const CUtensorMap& tb_lo = TM.b_lo;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, kz = blockIdx.z;
     constexpr int kBK = BF ? kRowBytes / 2 : kRowBytes / 4;  // K elements per k-block
@@ -167,17 +161,10 @@ __global__ void __launch_bounds__(128, 1)
     const unsigned base = (su32(tc_smem) + 1023u) & ~1023u;  // 1024-byte aligned tiles
     const unsigned full0 = su32(&bars[0]), empty0 = su32(&bars[kTcStages]),
                    done = su32(&bars[2 * kTcStages]);
-    unsigned* err = &A.ctl->error;
-    // switch mode: the tile needs the correction products when any of its
-    // columns' instances has switched (uniform over the block)
-    bool corr = A.x3 != 0;
-    if (A.adapt) {
-        const int col = n0 + tid;  // kBN == blockDim.x
-        corr = __syncthreads_or(col < A.N && A.px3[col / 3] != 0) != 0;
-    }
     const bool two_acc = A.adapt != 0;  // main and correction accumulators
     const uint32_t tcols = two_acc ? 2 * kBN : kBN;
-
+    // tensor memory and barriers do not depend on the previous kernel: set
+    // them up while it drains (programmatic dependent launch)
     if (warp == 0) {  // tensor memory for the 128 x 128 float32 accumulator(s)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          su32(&tmem_slot)),
@@ -196,6 +183,20 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    griddep_wait();
+    const int stage = A.ctl->stage;  // rho stage of this QP solve (the batch is in step)
+    const CUtensorMap& ta_hi = TM.a_hi[stage];
+    const CUtensorMap& ta_lo = TM.a_lo[stage];
+    const CUtensorMap& tb_hi = TM.b_hi;
+    const CUtensorMap& tb_lo = TM.b_lo;
+    unsigned* err = &A.ctl->error;
+    // switch mode: the tile needs the correction products when any of its
+    // columns' instances has switched (uniform over the block)
+    bool corr = A.x3 != 0;
+    if (A.adapt) {
+        const int col = n0 + tid;  // kBN == blockDim.x
+        corr = __syncthreads_or(col < A.N && A.px3[col / 3] != 0) != 0;
+    }
     const uint32_t tmem = tmem_slot;
     const uint32_t tmem_c = two_acc ? tmem + (uint32_t)kBN : tmem;  // correction accumulator
     const unsigned tx_bytes = (unsigned)((corr ? 4 : 2) * kTileBytes);
