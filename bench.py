@@ -823,17 +823,22 @@ def main():
         hx = torch.empty((B, 3, n, 11)).pin_memory()
         hr = torch.empty((B,)).pin_memory()
         hk = torch.empty((B,), dtype=torch.int32).pin_memory()
+
+        def e2e_solve():
+            s.copy_(hs, non_blocking=True)
+            g.copy_(hg, non_blocking=True)
+            pl.solve(s, g, K, out=out)
+            hx.copy_(out[0], non_blocking=True)
+            hr.copy_(out[1], non_blocking=True)
+            hk.copy_(out[2], non_blocking=True)
+
+        e2e_solve()  # warm-up of the same path (first use of the pinned buffers)
         flush.fill_(2.0)
         torch.cuda.synchronize()
         barrier()
         f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
         f0.record(stream)
-        s.copy_(hs, non_blocking=True)
-        g.copy_(hg, non_blocking=True)
-        pl.solve(s, g, K, out=out)
-        hx.copy_(out[0], non_blocking=True)
-        hr.copy_(out[1], non_blocking=True)
-        hk.copy_(out[2], non_blocking=True)
+        e2e_solve()
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_max = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
