@@ -620,6 +620,19 @@ amto_status amto_server_submit(amto_server server, const amto_request* req, uint
 amto_status amto_server_poll(amto_server server, uint64_t ticket, int wait_ms, float* xi_out,
                              amto_result_info* info);
 
+/* One step of the shared-budget admission policy (AMTO_ADMIT_SHARED) on a
+ * description of the served counts, with no device work: the server applies
+ * the same step between chunks.  Inputs per count (host arrays of n_counts,
+ * 1..32): slot capacity, resident requests (<= slots), queued requests, fair
+ * share and largest capacity in slots (slots <= max_capacity <= 65535), and
+ * device bytes per resident instance; budget in bytes.  slots_out (host
+ * [n_counts]) receives the capacities after the step (unchanged counts keep
+ * theirs).  Errors: EINVAL. */
+amto_status amto_admission_step(int n_counts, const int* slots, const int* active,
+                                const int* queued, const int* fair_slots, const int* max_capacity,
+                                const unsigned long long* bytes_per_instance,
+                                unsigned long long budget, int* slots_out);
+
 /* Counters of the server (completed requests and their iterations, chunks). */
 amto_status amto_server_stats(amto_server server, amto_server_stats_t* out);
 

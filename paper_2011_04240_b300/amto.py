@@ -143,6 +143,9 @@ SIGNATURES = {
     "amto_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P,
                                         ctypes.POINTER(ResultInfo)]),
     "amto_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "amto_admission_step": (ctypes.c_int, [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5 +
+                            [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_ulonglong,
+                             ctypes.POINTER(ctypes.c_int)]),
     "amto_server_destroy": (None, [_P]),
     "amto_last_error": (ctypes.c_char_p, []),
     "amto_version": (ctypes.c_char_p, []),
@@ -258,6 +261,19 @@ def tune(params: Params, batch: int, iters: int = 20) -> dict:
     ent = [(r.entries[i].tile_group, r.entries[i].tile_time_blocks, r.entries[i].apply_mode,
             r.entries[i].loop_mode, r.entries[i].us_per_iteration) for i in range(r.n_entries)]
     return {"best": ent[r.best][:4], "entries": ent}
+
+
+def admission_step(slots, active, queued, fair_slots, max_capacity, bytes_per_instance,
+                   budget: int) -> list:
+    """One step of the server's shared-budget admission policy on a description
+    of the served counts (no device work); returns the capacities after it."""
+    k = len(slots)
+    ints = lambda v: (ctypes.c_int * k)(*[int(x) for x in v])  # noqa: E731
+    out = (ctypes.c_int * k)()
+    per = (ctypes.c_ulonglong * k)(*[int(x) for x in bytes_per_instance])
+    _check(load().amto_admission_step(k, ints(slots), ints(active), ints(queued),
+                                      ints(fair_slots), ints(max_capacity), per, int(budget), out))
+    return list(out)
 
 
 def tune_cache_save(path: str) -> None:

@@ -36,6 +36,14 @@
 
 namespace amto {
 
+// A served count's state as the admission policy sees it: slot capacity,
+// resident and queued requests, fair share and largest capacity (slots), and
+// device bytes per resident instance.
+struct AdmitState {
+    int S, active, queued, fair, cap;
+    size_t per;
+};
+
 // Device bytes of one resident instance of a plan (the state amto_create
 // allocates per unit of max_batch).
 size_t instance_bytes(int n, int m, int degree, unsigned bc_mask, int precision, int proj_mode) {
@@ -363,6 +371,62 @@ int pow2_at_least(int v) {
     return q;
 }
 
+}  // namespace
+
+// One step of the shared-budget policy (see rebalance) on the counts' state,
+// with no device work: the capacity changes to make, in order (donors, then
+// the growing count; empty when nothing changes).
+std::vector<std::pair<int, int>> admission_step(const std::vector<AdmitState>& g, size_t budget,
+                                                size_t used) {
+    std::vector<std::pair<int, int>> out;
+    int gi = -1;
+    long long unmet_best = 0;
+    for (int i = 0; i < (int)g.size(); ++i) {
+        const long long unmet = (long long)g[i].queued - (g[i].S - g[i].active);
+        if (g[i].S < g[i].cap && unmet > unmet_best) {
+            unmet_best = unmet;
+            gi = i;
+        }
+    }
+    if (gi < 0) return out;
+    const AdmitState& G = g[gi];
+    const int target = std::min(G.cap, std::max(2 * G.S, pow2_at_least(G.active + G.queued)));
+    // donors, most reclaimable bytes first (ties: lower index)
+    std::vector<std::pair<size_t, int>> donors;
+    size_t room = budget > used ? budget - used : 0, avail = room;
+    for (int h = 0; h < (int)g.size(); ++h) {
+        if (h == gi) continue;
+        const AdmitState& H = g[h];
+        int floor_h = H.queued == 0
+                          ? std::max(std::min(8, H.fair), pow2_at_least(std::max(H.active, 1)))
+                          : std::max(H.fair, H.active);
+        floor_h = std::min(floor_h, H.S);
+        if (H.S - floor_h >= std::max(1, H.S / 4)) {
+            donors.push_back({(size_t)(H.S - floor_h) * H.per, h});
+            avail += (size_t)(H.S - floor_h) * H.per;
+        }
+    }
+    // grow by a quarter of the capacity at least, or not at all
+    const int reach = (int)std::min<size_t>((size_t)target, (size_t)G.S + avail / G.per);
+    if (reach < G.S + std::max(1, G.S / 4)) return out;
+    const size_t need = (size_t)(reach - G.S) * G.per;
+    std::stable_sort(donors.begin(), donors.end(),
+                     [](const std::pair<size_t, int>& a, const std::pair<size_t, int>& b) {
+                         return a.first > b.first;
+                     });
+    for (const auto& d : donors) {
+        if (room >= need) break;
+        const AdmitState& H = g[d.second];
+        out.push_back({d.second, H.S - (int)(d.first / H.per)});
+        room += d.first;
+    }
+    const int S = (int)std::min<size_t>((size_t)reach, (size_t)G.S + room / G.per);
+    if (S > G.S) out.push_back({gi, S});
+    return out;
+}
+
+namespace {
+
 // Shared memory budget (between chunks, every stream idle).  The count with
 // the most queued requests beyond its free slots doubles its capacity (at
 // least to the next power of two above its resident and queued requests; at
@@ -374,53 +438,24 @@ int pow2_at_least(int v) {
 // a count grows only by a quarter of its capacity or more.  At most one count
 // grows per chunk.
 amto_status rebalance(amto_server_s* sv) {
-    Group* grow = nullptr;
-    size_t unmet_best = 0;
+    std::vector<AdmitState> st;
     for (auto& gp : sv->groups) {
-        Group& g = *gp;
-        const size_t freeslots = (size_t)(g.S - g.active);
-        if (g.S < g.cap && g.queue.size() > freeslots &&
-            g.queue.size() - freeslots > unmet_best) {
-            unmet_best = g.queue.size() - freeslots;
-            grow = &g;
+        const Group& g = *gp;
+        st.push_back({g.S, g.active, (int)std::min<size_t>(g.queue.size(), 1u << 30), g.fair,
+                      g.cap, g.per});
+    }
+    const auto steps = admission_step(st, sv->budget, sv->used);
+    for (size_t k = 0; k < steps.size(); ++k) {
+        Group& g = *sv->groups[steps[k].first];
+        int S = steps[k].second;
+        if (k + 1 == steps.size() && S > g.S) {  // the growing count: what is actually free
+            const size_t room = sv->budget > sv->used ? sv->budget - sv->used : 0;
+            S = (int)std::min<size_t>((size_t)S, (size_t)g.S + room / g.per);
+            if (S <= g.S) break;
         }
+        const amto_status r = group_resize(sv, g, S);
+        if (r != AMTO_OK) return r;
     }
-    if (!grow) return AMTO_OK;
-    Group& g = *grow;
-    const int target =
-        std::min(g.cap, std::max(2 * g.S, pow2_at_least(g.active + (int)g.queue.size())));
-    // donors, most reclaimable bytes first
-    std::vector<std::pair<size_t, Group*>> donors;
-    size_t room = sv->budget > sv->used ? sv->budget - sv->used : 0, avail = room;
-    for (auto& hp : sv->groups) {
-        Group& h = *hp;
-        if (&h == &g) continue;
-        int floor_h = h.queue.empty()
-                          ? std::max(std::min(8, h.fair), pow2_at_least(std::max(h.active, 1)))
-                          : std::max(h.fair, h.active);
-        floor_h = std::min(floor_h, h.S);
-        if (h.S - floor_h >= std::max(1, h.S / 4)) {
-            donors.push_back({(size_t)(h.S - floor_h) * h.per, &h});
-            avail += (size_t)(h.S - floor_h) * h.per;
-        }
-    }
-    // grow by a quarter of the capacity at least, or not at all
-    const int reach = (int)std::min<size_t>((size_t)target, (size_t)g.S + avail / g.per);
-    if (reach < g.S + std::max(1, g.S / 4)) return AMTO_OK;
-    const size_t need = (size_t)(reach - g.S) * g.per;
-    std::sort(donors.begin(), donors.end(),
-              [](const std::pair<size_t, Group*>& a, const std::pair<size_t, Group*>& b) {
-                  return a.first > b.first;
-              });
-    for (auto& d : donors) {
-        if (room >= need) break;
-        Group& h = *d.second;
-        amto_status st = group_resize(sv, h, h.S - (int)(d.first / h.per));
-        if (st != AMTO_OK) return st;
-        room = sv->budget > sv->used ? sv->budget - sv->used : 0;
-    }
-    const int S = (int)std::min<size_t>((size_t)reach, (size_t)g.S + room / g.per);
-    if (S > g.S) return group_resize(sv, g, S);
     return AMTO_OK;
 }
 
@@ -757,6 +792,35 @@ amto_status amto_server_poll(amto_server sv, uint64_t ticket, int wait_ms, float
     const amto_status st = (amto_status)r.status;
     sv->results.erase(it);
     return st;
+}
+
+amto_status amto_admission_step(int n_counts, const int* slots, const int* active,
+                                const int* queued, const int* fair_slots, const int* max_capacity,
+                                const unsigned long long* bytes_per_instance,
+                                unsigned long long budget, int* slots_out) {
+    clear_error();
+    if (n_counts < 1 || n_counts > 32 || !slots || !active || !queued || !fair_slots ||
+        !max_capacity || !bytes_per_instance || !slots_out) {
+        set_error("invalid argument: 1..32 counts and every array are required");
+        return AMTO_EINVAL;
+    }
+    std::vector<AdmitState> st;
+    size_t used = 0;
+    for (int i = 0; i < n_counts; ++i) {
+        if (slots[i] < 1 || active[i] < 0 || active[i] > slots[i] || queued[i] < 0 ||
+            fair_slots[i] < 1 || max_capacity[i] < slots[i] || max_capacity[i] > 65535 ||
+            bytes_per_instance[i] == 0) {
+            set_error("invalid argument: need 0 <= active <= slots <= max_capacity <= 65535, "
+                      "queued >= 0, fair_slots >= 1 and bytes_per_instance > 0");
+            return AMTO_EINVAL;
+        }
+        st.push_back({slots[i], active[i], queued[i], fair_slots[i], max_capacity[i],
+                      (size_t)bytes_per_instance[i]});
+        used += (size_t)slots[i] * (size_t)bytes_per_instance[i];
+    }
+    for (int i = 0; i < n_counts; ++i) slots_out[i] = slots[i];
+    for (const auto& r : admission_step(st, (size_t)budget, used)) slots_out[r.first] = r.second;
+    return AMTO_OK;
 }
 
 amto_status amto_server_stats(amto_server sv, amto_server_stats_t* out) {
