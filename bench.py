@@ -534,6 +534,8 @@ def headline_summary(ex):
              "fp32_ii_s": _sig(r["plain_fp32_per_instance"]["inst_iter_per_s"]),
              "fp32_res": _sig(r["plain_fp32_per_instance"]["resid_max"], 2)}
             for r in ex["serving"]]
+    if "structured_apply" in ex:
+        out["structured_apply_ii_s"] = _sig(ex["structured_apply"]["value"])
     if "mixed" in ex:
         mx = ex["mixed"]
         out["mixed_ii_s"] = {k: _sig(mx[k]["value"]) for k in
@@ -659,6 +661,35 @@ def planar_compare(B=256, n=32, K=40):
         pl.close()
     return {"workload": f"{B} x {n} agents, random 12x12 m plane / 12x12x6 m box, m=100, "
                         "literal projection, TF32X3 apply", "unit": UNIT, **out}
+
+
+def structured_apply(probs, s, g, K, flush, dense_value):
+    """The headline workload with the structured K^-1 apply (Kronecker form of
+    Remarks 1-2, float32, one block per instance and axis) in place of the
+    dense tensor-core product: one untimed solve, L2 flushed, one timed solve
+    of K iterations, as the headline."""
+    import torch
+    from paper_2011_04240_b300 import Planner, amto
+    p0, B = probs[0], len(probs)
+    pl = Planner(p0.n, p0.m, p0.T, p0.a, p0.b, p0.rho, p0.degree, proj_mode=amto.PROJ_NOLAMBDA,
+                 precision=amto.PREC_FP32, max_batch=B, apply_mode=amto.APPLY_KRONECKER)
+    out = (torch.empty((B, 3, p0.n, 11), device="cuda"), torch.empty((B,), device="cuda"),
+           torch.empty((B,), device="cuda", dtype=torch.int32))
+    pl.solve(s, g, K, out=out)
+    flush.fill_(3.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    pl.solve(s, g, K, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    assert int(out[2].sum().item()) == B * K
+    pl.close()
+    value = B * K / (ms / 1e3)
+    return {"workload": "the headline's batch and iteration count",
+            "apply": "structured (Kronecker) K^-1 apply, float32", "unit": UNIT,
+            "value": value, "ms_per_step": ms / K, "vs_dense": value / dense_value}
 
 
 def circle4_latency(reps=5):
@@ -919,6 +950,7 @@ def main():
             extras["circle4_latency"] = circle4_latency()
             extras["obstacles"] = obstacle_scaling()
             extras["planar"] = planar_compare()
+            extras["structured_apply"] = structured_apply(probs, s, g, K, flush, B * K / (ms / 1e3))
             extras["serving"] = [
                 serving_compare(r, SWEEP_SECONDS, args.precision, seq_cap=SWEEP_SEQ_CAP,
                                 rho_schedule=(10, 100 ** (1 / 9), 10) if r == 1000.0 else None)
