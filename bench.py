@@ -22,7 +22,6 @@ import os
 import re
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -259,19 +258,41 @@ def profile_traffic(n, batch, form):
     return float(mb.group(1)) * batch
 
 
+def keep_busy(seconds, fn):
+    """Runs `fn` (untimed GPU work) back to back for about `seconds`.  After
+    an idle spell a B300 ran the 256 x 64 solve 4-7 % slower until it had
+    been busy for a few hundred ms (measured: ten back-to-back solves right
+    after a 0.3 s pause still ran at 2.19-2.23 M instance-iterations/s, after
+    ~0.5 s of solves 2.29-2.32 M), so every timed leg starts from a busy GPU."""
+    import torch
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        fn()
+        n += 1
+        if n % 8 == 0:
+            torch.cuda.synchronize()
+            if time.perf_counter() - t0 >= seconds:
+                break
+    torch.cuda.synchronize()
+
+
 class ClockSampler:
     """Samples SM clock, power and throttle reasons with nvidia-smi (every
-    50 ms) while the timed region runs; keeps the samples taken under load."""
+    50 ms) while the timed region runs; keeps the samples taken under load.
+    The samples wait in the pipe (a few KB per second) and are read after
+    the process stops: no reader thread competes with the timed code for
+    the interpreter."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, warm=None):
         self.index = index
         self.rows = []
         self._p = None
-        self._t = None
+        self._warm = warm  # untimed GPU work run while nvidia-smi starts
 
     def __enter__(self):
         try:
@@ -279,28 +300,27 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self._t = threading.Thread(target=self._read, daemon=True)
-            self._t.start()
-            time.sleep(0.3)
         except Exception:
             self._p = None
+        if self._warm is not None:
+            self._warm()
+        else:
+            time.sleep(0.3)
         return self
-
-    def _read(self):
-        for line in self._p.stdout:
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
 
     def __exit__(self, *a):
         if self._p:
             time.sleep(0.1)
             self._p.terminate()
             try:
-                self._p.wait(timeout=5)
+                out = self._p.communicate(timeout=5)[0]
             except Exception:
                 self._p.kill()
-            self._t.join(timeout=5)
+                out = self._p.communicate()[0]
+            for line in (out or "").splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    self.rows.append(parts)
 
     def summary(self):
         def num(x):
@@ -454,8 +474,7 @@ def mixed_batch(args, n_instances=512, sizes=(8, 16, 24, 32), prec="fp32", tile_
 
     if args.trace:
         mx.set_trace(True)
-    with ClockSampler(0) as clk:
-        mx.solve(starts, goals, K, out=outs)  # untimed: the GPU leaves the sampler's idle start
+    with ClockSampler(0, warm=lambda: keep_busy(0.5, lambda: mx.solve(starts, goals, K, out=outs))) as clk:
         ms_mixed = timed(lambda: mx.solve(starts, goals, K, out=outs))
     its = sum(int(o[2].sum().item()) for o in outs)
     assert its == n_instances * K, (its, n_instances * K)
@@ -675,10 +694,9 @@ def structured_apply(probs, s, g, K, flush, dense_value):
                  precision=amto.PREC_FP32, max_batch=B, apply_mode=amto.APPLY_KRONECKER)
     out = (torch.empty((B, 3, p0.n, 11), device="cuda"), torch.empty((B,), device="cuda"),
            torch.empty((B,), device="cuda", dtype=torch.int32))
-    pl.solve(s, g, K, out=out)
-    flush.fill_(3.0)
-    torch.cuda.synchronize()
+    keep_busy(0.5, lambda: pl.solve(s, g, K, out=out))
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    flush.fill_(3.0)  # (as the headline: enqueued before the start event)
     e0.record()
     pl.solve(s, g, K, out=out)
     e1.record()
@@ -822,6 +840,10 @@ def main():
     pl.solve(s, g, max(args.warmup, 3), out=out)
     torch.cuda.synchronize()
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB, twice L2
+    # written once now: the first write to the fresh buffer slowed the solve
+    # after it by ~0.07 ms (measured on B300), a one-off cost of the buffer
+    flush.fill_(0.0)
+    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
@@ -831,14 +853,15 @@ def main():
     if args.trace:
         pl.set_trace(True)
     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-    with ClockSampler(local) as clk:
-        # an untimed solve right before the timed one: the sampler's start-up
-        # left the GPU idle for 0.3 s, and the first solve after an idle spell
-        # runs 0.05-0.2 ms slower (measured on B300) while the clocks come up
-        pl.solve(s, g, K, out=out)
-        flush.fill_(1.0)  # the timed solve starts with nothing of its state in L2
+    # untimed solves of the same workload for ~0.5 s while the sampler starts
+    # (see keep_busy), then the timed one
+    with ClockSampler(local, warm=lambda: keep_busy(0.5, lambda: pl.solve(s, g, K, out=out))) as clk:
         barrier()
         torch.cuda.synchronize()
+        # the timed solve starts with nothing of its state in L2; the flush is
+        # enqueued before the start event, so the GPU writes it while the host
+        # enqueues the solve (the start event does not wait on host work)
+        flush.fill_(1.0)
         e0.record(stream)
         pl.solve(s, g, K, out=out)
         e1.record(stream)
@@ -868,7 +891,7 @@ def main():
             hr.copy_(out[1], non_blocking=True)
             hk.copy_(out[2], non_blocking=True)
 
-        e2e_solve()  # warm-up of the same path (first use of the pinned buffers)
+        keep_busy(0.5, e2e_solve)  # the same path untimed (also the pinned buffers' first use)
         flush.fill_(2.0)
         torch.cuda.synchronize()
         barrier()
