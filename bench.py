@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--precision", default="tf32x3",
                     choices=["fp32", "tf32x3", "bf16x3", "tf32", "bf16"],
                     help="arithmetic of the cached-inverse apply (pair step is float32)")
+    ap.add_argument("--apply", default="dense", choices=["dense", "structured"],
+                    help="K^-1 apply of the timed plan: the dense product (default) or the "
+                         "structured Kronecker form (float32, inside the right-hand-side kernel)")
     ap.add_argument("--multipliers", default="auto", choices=["auto", "pairs", "aggregate"],
                     help="multiplier form of the plan (auto: aggregated for this reading)")
     ap.add_argument("--trace", action="store_true",
@@ -175,7 +178,9 @@ def bench_config(args, world):
                         "GPU, degree-10 Bernstein, m=100, T=8 s, a=0.6, b=1.2, rho=1, "
                         "lambda-free projection, fixed iterations",
             "batch_per_gpu": args.batch, "agents": args.agents, "m": 100,
-            "apply_precision": args.precision,
+            "apply": "dense K^-1 product" if args.apply == "dense"
+                     else "structured (Kronecker) K^-1",
+            "apply_precision": args.precision if args.apply == "dense" else "fp32",
             "multipliers": "per pair" if args.multipliers == "pairs"
                            else "aggregated (A_fc^T lambda)",
             "l2": "L2 flushed (256 MiB write) before the timed solve; the per-iteration state "
@@ -826,11 +831,13 @@ def main():
 
     probs = workload(args, rank)
     n, m, B, K = probs[0].n, probs[0].m, len(probs), args.steps
-    prec = PRECISIONS[args.precision]
+    structured = args.apply == "structured"
+    prec = amto.PREC_FP32 if structured else PRECISIONS[args.precision]
     mult = {"auto": amto.MULT_AUTO, "pairs": amto.MULT_PAIRS,
             "aggregate": amto.MULT_AGGREGATE}[args.multipliers]
     pl = Planner(n, m, probs[0].T, probs[0].a, probs[0].b, probs[0].rho, probs[0].degree,
-                 proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B, multipliers=mult)
+                 proj_mode=amto.PROJ_NOLAMBDA, precision=prec, max_batch=B, multipliers=mult,
+                 apply_mode=amto.APPLY_KRONECKER if structured else amto.APPLY_AUTO)
     s_np, g_np = W.stack(probs)
     s = torch.from_numpy(s_np).cuda()
     g = torch.from_numpy(g_np).cuda()
