@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py: the per-pair-form byte count, the
 pair-kernel traffic lookup keyed by the kernel's source, and the compact
-headline summary at the end of the JSON line."""
+headline summary at the end of the JSON line, and the clock sampler (samples read
+once nvidia-smi is stopped, warm work run while it starts)."""
 import os
 import shutil
 
@@ -76,3 +77,40 @@ def test_headline_summary_rounds_and_orders():
     assert out["precision"]["xi_err"]["fp32"] == [3.0e-6, 6.0e-6]
     assert out["precision"]["res200"]["fp32"] == 0.3
     assert bench.headline_summary({}) == {}
+
+
+class _FakeSmi:
+    """Stands in for the nvidia-smi process: its samples come back from
+    communicate() once it is stopped."""
+    OUT = ("0, 2032, 2032, 455.30, 100, Not Active, Not Active, Not Active, Active\n"
+           "0, 1980, 2032, 300.00, 98, Not Active, Not Active, Not Active, Not Active\n"
+           "0, 2032, 2032, 120.00, 0, Not Active, Not Active, Not Active, Not Active\n"
+           "garbage line\n")
+
+    def __init__(self, *a, **k):
+        self.stopped = False
+
+    def terminate(self):
+        self.stopped = True
+
+    def communicate(self, timeout=None):
+        assert self.stopped  # read only after the process is told to stop
+        return self.OUT, None
+
+    def kill(self):
+        self.stopped = True
+
+
+def test_clock_sampler_reads_after_stopping_and_runs_the_warm_work(monkeypatch):
+    monkeypatch.setattr(bench.subprocess, "Popen", _FakeSmi)
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    ran = []
+    with bench.ClockSampler(0, warm=lambda: ran.append(1)) as clk:
+        assert clk.rows == []  # nothing is read while the timed code runs
+    assert ran == [1]
+    assert len(clk.rows) == 3
+    sm = clk.summary()
+    # samples under load (utilisation > 0): median SM clock, max power, reasons seen
+    assert sm["samples"] == 2 and sm["sm_max_mhz"] == 2032.0
+    assert sm["sm_mhz"] in (1980.0, 2032.0) and sm["power_w_max"] == 455.3
+    assert sm["reasons"] == ["sw_power_cap"]
