@@ -638,7 +638,7 @@ def obstacle_scaling(counts=(0, 4, 8, 16, 32), B=256, n=16, K=40):
         if n_obs:
             pl.set_obstacles(torch.from_numpy(np.stack([o for _, o in pairs])).cuda())
         pl.solve(s, g, 3)
-        torch.cuda.synchronize()
+        keep_busy(0.3, lambda: pl.solve(s, g, 5))
         ts = []
         for k in (5, 5 + K):
             e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -670,7 +670,7 @@ def planar_compare(B=256, n=32, K=40):
         g = torch.from_numpy(g_np).cuda()
         pl = Planner(n, 100, 8.0, max_batch=B, planar=planar, precision=amto.PREC_TF32X3)
         pl.solve(s, g, 3)
-        torch.cuda.synchronize()
+        keep_busy(0.3, lambda: pl.solve(s, g, 5))
         ts = []
         for k in (5, 5 + K):
             e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
